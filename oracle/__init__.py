@@ -1,0 +1,205 @@
+"""ctypes front end of the CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / ``--impl reference`` leg are the only callers.
+The product library never imports this package.
+
+The oracle is single-threaded plain C in double precision.  ``build()``
+compiles it with gcc; ``Oracle`` wraps one scene + edit.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+TECH_PT, TECH_T1, TECH_T2, TECH_T3, TECH_T7 = 0, 1, 2, 3, 7
+MASK_ALL = 0b1111                  # bit 0: T1, bit 1: T2, bit 2: T3, bit 3: T7
+
+# status codes of a base path's mapping (see oracle.c)
+MAP_ACCEPT, MAP_INVALID, MAP_REJECT_NODYN, MAP_REJECT_MULTI, MAP_REJECT_INVERT, MAP_REJECT_JAC = \
+    range(6)
+
+RECORD_DTYPE = np.dtype([
+    ("root", "<u4"), ("tech", "<i4"), ("frame", "<i4"), ("sa", "<i4"), ("sb", "<i4"),
+    ("pix_a", "<i4"), ("pix_b", "<i4"), ("_pad0", "<i4"),
+    ("va", "<f8", 3), ("vb", "<f8", 3), ("status", "<i4"), ("_pad1", "<i4"),
+    ("Pg", "<f8"), ("Py", "<f8"), ("J", "<f8"),
+])
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        P = C.c_void_p
+        L.oracle_create.restype = P
+        L.oracle_create.argtypes = [P, C.c_int, P, P, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int,
+                                    P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                    C.c_double]
+        L.oracle_set_edit.argtypes = [P, P, P, P, P]
+        L.oracle_set_brute_force.argtypes = [P, C.c_int]
+        L.oracle_destroy.argtypes = [P]
+        L.oracle_render_residual.argtypes = [P, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32,
+                                             C.c_int, P, P]
+        L.oracle_render_primal.argtypes = [P, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
+                                           C.c_uint32, P]
+        L.oracle_dump.restype = C.c_int64
+        L.oracle_dump.argtypes = [P, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
+                                  C.c_uint32, C.c_int, P, C.c_int64]
+        L.oracle_record_size.restype = C.c_int
+        L.oracle_closest_hit.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P, P]
+        L.oracle_philox4x32_10.argtypes = [P, P, P]
+        L.oracle_bsdf.argtypes = [P, P, P, P, P, P]
+        L.oracle_bsdf_sample.restype = C.c_int
+        L.oracle_bsdf_sample.argtypes = [P, P, P, C.c_double, C.c_double, P, P]
+        L.oracle_tangent_frame.argtypes = [P, P, P]
+        L.oracle_check_mapping.argtypes = [P, C.c_int, C.c_int, C.c_uint32, C.c_uint64,
+                                           C.c_uint32, C.c_uint32, P]
+        assert L.oracle_record_size() == RECORD_DTYPE.itemsize, "record layout mismatch"
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def philox4x32_10(counter, key):
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def bsdf(mat_row, n, wi, wo):
+    m = np.ascontiguousarray(mat_row, dtype=np.float32)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (n, wi, wo)]
+    rho = np.zeros(3)
+    pdf = np.zeros(1)
+    lib().oracle_bsdf(_p(m), _p(arrs[0]), _p(arrs[1]), _p(arrs[2]), _p(rho), _p(pdf))
+    return rho, float(pdf[0])
+
+
+def bsdf_sample(mat_row, n, wc, u1, u2):
+    m = np.ascontiguousarray(mat_row, dtype=np.float32)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    wc = np.ascontiguousarray(wc, dtype=np.float64)
+    wo = np.zeros(3)
+    ub = np.zeros(2)
+    ok = lib().oracle_bsdf_sample(_p(m), _p(n), _p(wc), float(u1), float(u2), _p(wo), _p(ub))
+    return (wo, ub) if ok else (None, None)
+
+
+def tangent_frame(n):
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    t = np.zeros(3)
+    b = np.zeros(3)
+    lib().oracle_tangent_frame(_p(n), _p(t), _p(b))
+    return t, b
+
+
+class Oracle:
+    """One scene with one edit, held by the C oracle."""
+
+    def __init__(self, scene, edit=None, brute_force=False):
+        self.scene = scene
+        L = lib()
+        self._keep = [np.ascontiguousarray(scene.static_vertices, dtype=np.float32),
+                      np.ascontiguousarray(scene.static_triangles, dtype=np.uint32),
+                      np.ascontiguousarray(scene.static_material, dtype=np.uint32),
+                      np.ascontiguousarray(scene.dyn_vertices, dtype=np.float32),
+                      np.ascontiguousarray(scene.dyn_triangles, dtype=np.uint32),
+                      np.ascontiguousarray(scene.materials, dtype=np.float32),
+                      scene.camera.as_array()]
+        sv, st, sm, dv, dt, mats, cam = self._keep
+        self.h = L.oracle_create(_p(sv), len(sv), _p(st), _p(sm), len(st), _p(dv), len(dv),
+                                 _p(dt), len(dt), _p(mats), len(mats), _p(cam),
+                                 scene.camera.width, scene.camera.height, scene.max_depth,
+                                 scene.alpha_min, scene.d_min, scene.jacobian_max)
+        if brute_force:
+            L.oracle_set_brute_force(self.h, 1)
+        if edit is not None:
+            self.set_edit(edit)
+
+    def set_edit(self, edit):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32).ravel()
+                for a in (edit.M1, edit.M2, edit.mat1, edit.mat2)]
+        self._edit = arrs
+        lib().oracle_set_edit(self.h, *[_p(a) for a in arrs])
+
+    def close(self):
+        if self.h:
+            lib().oracle_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.scene.camera.height, self.scene.camera.width, 3)
+
+    def n_roots(self, spp):
+        return spp * self.scene.camera.width * self.scene.camera.height
+
+    def render_residual(self, spp, seed, root_begin=0, root_end=None, tech_mask=MASK_ALL,
+                        counters=False):
+        img = np.zeros(self.shape)
+        cnt = np.zeros(8, dtype=np.int64)
+        r1 = self.n_roots(spp) if root_end is None else root_end
+        lib().oracle_render_residual(self.h, spp, seed, root_begin, r1, tech_mask, _p(img),
+                                     _p(cnt))
+        return (img, cnt) if counters else img
+
+    def render_primal(self, frame, spp, seed, root_begin=0, root_end=None):
+        img = np.zeros(self.shape)
+        r1 = self.n_roots(spp) if root_end is None else root_end
+        lib().oracle_render_primal(self.h, frame, spp, seed, root_begin, r1, _p(img))
+        return img
+
+    def dump(self, tech, frame, spp, seed, root_begin, root_end, tech_mask=MASK_ALL,
+             max_records=None):
+        L = lib()
+        n = L.oracle_dump(self.h, tech, frame, spp, seed, root_begin, root_end, tech_mask, None, 0)
+        cap = n if max_records is None else min(n, max_records)
+        rec = np.zeros(cap, dtype=RECORD_DTYPE)
+        L.oracle_dump(self.h, tech, frame, spp, seed, root_begin, root_end, tech_mask, _p(rec),
+                      cap)
+        return rec
+
+    def closest_hit(self, frame, origins, dirs):
+        o = np.ascontiguousarray(origins, dtype=np.float64)
+        d = np.ascontiguousarray(dirs, dtype=np.float64)
+        n = len(o)
+        t = np.zeros(n); prim = np.zeros(n, dtype=np.int32)
+        b1 = np.zeros(n); b2 = np.zeros(n)
+        lib().oracle_closest_hit(self.h, frame, n, _p(o), _p(d), _p(t), _p(prim), _p(b1), _p(b2))
+        return t, prim, b1, b2
+
+    def check_mapping(self, tech, frame, spp, seed, root_begin, root_end):
+        out = np.zeros(6)
+        lib().oracle_check_mapping(self.h, tech, frame, spp, seed, root_begin, root_end, _p(out))
+        return dict(pairs=int(out[0]), bad_inverse=int(out[1]), max_pos_err=out[2],
+                    max_jac_err=out[3], fd_checked=int(out[4]), max_fd_err=out[5])
