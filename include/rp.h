@@ -1,0 +1,201 @@
+/*
+ * rp.h -- C ABI of librp, a GB300 (sm_103a) implementation of residual path
+ * integrals for re-rendering (Xu, Li, Georgiev, Hedstrom, Ramamoorthi,
+ * EGSR 2024, arXiv 2406.16302).
+ *
+ * Given a scene, an original frame (1) and an edit that produces frame 2
+ * (a rigid motion of one object, or a material change of it), the library
+ * estimates only the residual image I2 - I1 (Sec. 3.2, "The residual path
+ * integral"): Monte Carlo paths are rooted on the edited object and traced
+ * toward the camera and the lights (Sec. 4.1), each path is mapped into the
+ * other frame with its Jacobian (Sec. 5), weighted by the balance heuristic
+ * over all techniques (Sec. 4.3) and splatted.
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named `d_*` are device pointers; all others are host
+ *     pointers.  The caller owns every buffer it passes; the library owns
+ *     scenes and edits.
+ *   - Images are row-major [height][width][3] linear RGB radiance, row 0 at
+ *     the top.  Render calls ACCUMULATE into the caller's image.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Render and query calls are stream-ordered and asynchronous;
+ *     argument errors are returned synchronously, launch errors as
+ *     RP_ERR_CUDA.  rp_last_error() returns a thread-local message for the
+ *     last failing call.
+ *   - Every path is fixed by (scene, edit, spp, seed): random numbers come
+ *     from Philox4x32-10 counters keyed by (root, technique, frame, walk side,
+ *     step), never by call order.  Only the order of floating-point atomic
+ *     additions into the image varies between runs.
+ *   - The library never falls back to a CPU path: without a usable CUDA
+ *     device every call that needs one returns RP_ERR_CUDA.
+ */
+#ifndef RP_H
+#define RP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RP_OK = 0,
+    RP_ERR_INVALID_ARG = 1,
+    RP_ERR_OOM = 2,
+    RP_ERR_CUDA = 3,
+    RP_ERR_TIMEOUT = 4,
+    RP_ERR_UNSUPPORTED = 5
+} rp_status;
+
+/* techniques, as bits of a technique mask (Sec. 4.1 and 4.3) */
+#define RP_TECH_DYNAMIC_FROM_EMITTER 1u  /* (1): x_D, NEE to x_L, walk to the sensor */
+#define RP_TECH_DYNAMIC_FROM_SENSOR  2u  /* (2): x_D seen by the sensor, walk to the lights */
+#define RP_TECH_DYNAMIC_TWO_ENDS     4u  /* (3): x_D, cosine light side, BSDF eye side */
+#define RP_TECH_PATH_TRACING         8u  /* path tracing with static paths rejected */
+#define RP_TECH_ALL                 15u
+
+/* Material row: 12 floats
+ *   [type, albedo r g b, alpha, f0 r g b, emission r g b, unused]
+ * type 0 = Lambert (albedo / pi), 1 = GGX microfacet reflection (Walter et
+ * al. 2007: D = GGX, separable Smith masking, Schlick Fresnel with F0).
+ * Triangles are one-sided: the front side is cross(v1 - v0, v2 - v0).
+ * A triangle whose material has non-zero emission is an area light that
+ * emits from its front side. */
+#define RP_MATERIAL_FLOATS 12
+
+typedef struct {
+    /* static geometry, world space */
+    const float *static_vertices;      /* [n_static_vertices][3] */
+    uint32_t n_static_vertices;
+    const uint32_t *static_triangles;  /* [n_static_triangles][3] vertex indices */
+    const uint32_t *static_material;   /* [n_static_triangles] material index */
+    uint32_t n_static_triangles;
+    /* the edited (dynamic) object, object space; its material comes from the edit */
+    const float *dyn_vertices;         /* [n_dyn_vertices][3] */
+    uint32_t n_dyn_vertices;
+    const uint32_t *dyn_triangles;     /* [n_dyn_triangles][3] */
+    uint32_t n_dyn_triangles;
+    const float *materials;            /* [n_materials][RP_MATERIAL_FLOATS] */
+    uint32_t n_materials;
+    /* pinhole camera: position, look-at point, up vector, vertical field of
+     * view in degrees; a box pixel filter over width x height pixels */
+    float camera[10];
+    uint32_t width, height;
+    /* maximum number of path edges (Eq. pathcontribution with k - 1 <= max_depth) */
+    uint32_t max_depth;
+    /* reconnection thresholds alpha_min and d_min and the Jacobian threshold
+     * (Sec. 5, "Keep vertex the same" criteria 2 and 3, "Path rejection") */
+    float alpha_min, d_min, jacobian_max;
+} rp_scene_desc;
+
+typedef struct rp_scene_s rp_scene;
+typedef struct rp_edit_s rp_edit_handle;
+
+/* Build a scene: copies all host arrays, builds SAH BVHs for the static
+ * geometry and for the dynamic object (object space), sampling tables for
+ * the dynamic object's area (p(x_D), Sec. 4.1) and the emitters' area
+ * (p(x_L)), and uploads them to the current CUDA device.  Synchronous.
+ * Errors: RP_ERR_INVALID_ARG (null pointers, indices out of range, no
+ * emitter, no dynamic triangle, max_depth outside [2, 12], emissive dynamic
+ * material), RP_ERR_OOM, RP_ERR_CUDA. */
+rp_status rp_scene_create(const rp_scene_desc *desc, rp_scene **out);
+void rp_scene_destroy(rp_scene *scene);
+
+/* An edit: the dynamic object's object-to-world transform (row-major 3x4)
+ * and material row in frame 1 (original) and frame 2 (edited).  A rigid
+ * motion keeps the material ("Transform with object movement", Sec. 5); a
+ * material edit keeps the transform (Sec. 6, "Scene editing"); both may
+ * change at once.  Transforms must be rigid (orthonormal 3x3 part within
+ * 1e-4), else RP_ERR_UNSUPPORTED.  Synchronous, small upload. */
+typedef struct {
+    float M1[12], M2[12];
+    float mat1[RP_MATERIAL_FLOATS], mat2[RP_MATERIAL_FLOATS];
+} rp_edit_desc;
+
+rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out);
+void rp_edit_destroy(rp_edit_handle *edit);
+
+/* Residual image I2 - I1 (Eq. shiftmapped restricted to dynamic paths,
+ * Eq. difference_integral): N = spp * width * height roots for every
+ * technique in `tech_mask` and both frames; accumulated with FP64 atomics
+ * into d_out[height][width][3] (double).  Unbiased when tech_mask contains
+ * RP_TECH_PATH_TRACING.  Asynchronous on `stream`. */
+rp_status rp_render_residual(rp_scene *scene, const rp_edit_handle *edit, uint32_t spp,
+                             uint64_t seed, uint32_t tech_mask, double *d_out, void *stream);
+
+/* Same estimate written into a float32 image: accumulated in a library-owned
+ * FP64 scratch image, then added to d_out[height][width][3] (float).
+ * The scratch image is allocated on first use per scene and reused; calls on
+ * one scene must not overlap. */
+rp_status rp_render_residual_f32(rp_scene *scene, const rp_edit_handle *edit, uint32_t spp,
+                                 uint64_t seed, uint32_t tech_mask, float *d_out, void *stream);
+
+/* End-to-end convenience call with HOST buffers: uploads the edit, renders
+ * the residual and copies it into host_out[height][width][3] (double,
+ * overwritten, not accumulated).  Synchronous on `stream`. */
+rp_status rp_render_residual_host(rp_scene *scene, const rp_edit_desc *edit, uint32_t spp,
+                                  uint64_t seed, uint32_t tech_mask, double *host_out,
+                                  void *stream);
+
+/* Primal image of frame 1 or 2 by path tracing with next-event estimation
+ * (Eq. pathIntegral): the "PT from scratch" baseline of Sec. 6 and, with the
+ * same seed in both frames, correlated path tracing.  Accumulates into
+ * d_out (double).  Asynchronous. */
+rp_status rp_render_primal(rp_scene *scene, const rp_edit_handle *edit, int frame, uint32_t spp,
+                           uint64_t seed, double *d_out, void *stream);
+
+/* Per-sample records for roots [root_begin, root_end) of one technique
+ * (1, 2, 3 or 7 = path tracing) in one frame, for parity testing.  Each
+ * base path with non-zero contribution yields one record; d_count receives
+ * the number of records produced (may exceed capacity; only the first
+ * `capacity` are written).  Asynchronous. */
+typedef struct {
+    uint32_t root;
+    int32_t tech, frame;
+    int32_t sa, sb;          /* strategy: (t', s') walk lengths or path length */
+    int32_t pix_a, pix_b;    /* pixel of the base path and of the mapped path (-1: none) */
+    float va[3], vb[3];      /* the two splats */
+    int32_t status;          /* 0 accepted pair, 1 invalid mapped path, 2-5 rejected */
+    float Pg, Py, J;         /* MIS denominators of x and T(x), Jacobian */
+} rp_record;
+
+rp_status rp_dump_samples(rp_scene *scene, const rp_edit_handle *edit, int tech, int frame,
+                          uint32_t spp, uint64_t seed, uint32_t root_begin, uint32_t root_end,
+                          uint32_t tech_mask, rp_record *d_records, uint64_t capacity,
+                          unsigned long long *d_count, void *stream);
+
+/* Closest hits of n rays in frame 1 or 2 (static BVH and the dynamic BVH
+ * under that frame's transform; watertight ray/triangle test of Woop,
+ * Benthin and Wald 2013).  t = +inf and prim = -1 on a miss; prim numbers
+ * static triangles first, then the dynamic object's.  Asynchronous. */
+rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edit, int frame, uint32_t n,
+                           const float *d_origins, const float *d_dirs, float *d_t,
+                           int32_t *d_prim, float *d_b1, float *d_b2, void *stream);
+
+/* Philox4x32-10 on the device for n (counter[4], key[2]) pairs, for
+ * known-answer tests.  Asynchronous. */
+rp_status rp_philox(uint32_t n, const uint32_t *d_counters, const uint32_t *d_keys,
+                    uint32_t *d_out, void *stream);
+
+/* Work counters of the most recent render on a scene (synchronises the
+ * scene's last stream): roots, base paths splatted, rays traced by kind and
+ * BVH nodes / triangles visited, used for the traversal roofline. */
+typedef struct {
+    unsigned long long roots;
+    unsigned long long paths;
+    unsigned long long rays_closest, rays_shadow;
+    unsigned long long nodes_visited, tris_tested;
+    unsigned long long accepted, rejected;
+} rp_stats;
+
+rp_status rp_enable_stats(rp_scene *scene, int on);
+rp_status rp_get_stats(rp_scene *scene, rp_stats *out);
+
+/* Thread-local message describing the last error (empty string if none). */
+const char *rp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RP_H */

@@ -899,7 +899,7 @@ static void emit(sink *k, uint32_t root, int tech, int g, int sa, int sb, int pa
         r->vb[0] = vb.x; r->vb[1] = vb.y; r->vb[2] = vb.z;
         r->status = status; r->Pg = Pg; r->Py = Py; r->J = J;
     }
-    if (k->rec) ++*k->n_rec;
+    if (k->n_rec) ++*k->n_rec;
 }
 
 static int g_check_mode = 0;

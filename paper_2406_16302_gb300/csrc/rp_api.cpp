@@ -1,0 +1,502 @@
+// C ABI of librp (include/rp.h): scene and edit management, argument
+// checking and the stream-ordered launches of the path kernels.
+#include "../../include/rp.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bvh_build.h"
+#include "rp_internal.h"
+
+using namespace rp;
+
+namespace {
+
+thread_local std::string g_err;
+
+rp_status fail(rp_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+rp_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(RP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RP_CUDA(call, what)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
+    } while (0)
+
+rp_status need_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return fail(RP_ERR_CUDA, "no usable CUDA device (librp has no CPU fallback)");
+    return RP_OK;
+}
+
+template <class T>
+rp_status upload(const std::vector<T> &h, T **d) {
+    *d = nullptr;
+    if (h.empty()) return RP_OK;
+    cudaError_t e = cudaMalloc((void **)d, sizeof(T) * h.size());
+    if (e == cudaErrorMemoryAllocation) return fail(RP_ERR_OOM, "device allocation failed");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    RP_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice), "upload");
+    return RP_OK;
+}
+
+}  // namespace
+
+struct rp_scene_s {
+    DevScene S{};
+    std::vector<void *> allocs;
+    int bvh_depth_static = 0, bvh_depth_dyn = 0;
+    unsigned long long *d_stats = nullptr;
+    bool stats_on = false;
+    double *d_scratch = nullptr;   // FP64 image for the f32 and host entry points
+    cudaStream_t last_stream = nullptr;
+    ~rp_scene_s() {
+        for (void *p : allocs) cudaFree(p);
+        if (d_stats) cudaFree(d_stats);
+        if (d_scratch) cudaFree(d_scratch);
+    }
+};
+
+struct rp_edit_s {
+    DevEdit E{};
+};
+
+extern "C" const char *rp_last_error(void) { return g_err.c_str(); }
+
+static bool material_ok(const float *m) {
+    for (int i = 0; i < 11; ++i)
+        if (!std::isfinite(m[i])) return false;
+    int type = (int)m[0];
+    if (!(m[0] == 0.f || m[0] == 1.f)) return false;
+    if (type == 1 && !(m[4] > 0.f)) return false;
+    return true;
+}
+
+extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
+    if (!d || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (rp_status s = need_device()) return s;
+    if (!d->static_vertices || !d->static_triangles || !d->static_material || !d->dyn_vertices ||
+        !d->dyn_triangles || !d->materials)
+        return fail(RP_ERR_INVALID_ARG, "null array in scene description");
+    if (d->n_static_triangles == 0 || d->n_dyn_triangles == 0 || d->n_materials == 0)
+        return fail(RP_ERR_INVALID_ARG, "empty static geometry, dynamic object or material table");
+    if (d->width == 0 || d->height == 0 || (uint64_t)d->width * d->height > (1u << 26))
+        return fail(RP_ERR_INVALID_ARG, "image size out of range");
+    if (d->max_depth < 2 || d->max_depth > (uint32_t)kMaxDepth)
+        return fail(RP_ERR_INVALID_ARG, "max_depth must be in [2, 10]");
+    if (d->n_static_triangles + (uint64_t)d->n_dyn_triangles >= (1u << 30))
+        return fail(RP_ERR_INVALID_ARG, "too many triangles");
+    for (uint32_t i = 0; i < 3 * d->n_static_triangles; ++i)
+        if (d->static_triangles[i] >= d->n_static_vertices)
+            return fail(RP_ERR_INVALID_ARG, "static triangle index out of range");
+    for (uint32_t i = 0; i < d->n_static_triangles; ++i)
+        if (d->static_material[i] >= d->n_materials)
+            return fail(RP_ERR_INVALID_ARG, "static material index out of range");
+    for (uint32_t i = 0; i < 3 * d->n_dyn_triangles; ++i)
+        if (d->dyn_triangles[i] >= d->n_dyn_vertices)
+            return fail(RP_ERR_INVALID_ARG, "dynamic triangle index out of range");
+    for (uint32_t i = 0; i < d->n_materials; ++i)
+        if (!material_ok(d->materials + 12 * i))
+            return fail(RP_ERR_INVALID_ARG, "invalid material row");
+
+    const int ns = (int)d->n_static_triangles, nd = (int)d->n_dyn_triangles;
+    rp_scene *sc = new rp_scene_s();
+    DevScene &S = sc->S;
+    auto keep = [&](void *p) { if (p) sc->allocs.push_back(p); };
+
+    BuiltBVH bs = build_bvh(d->static_vertices, d->static_triangles, ns, 0);
+    BuiltBVH bd = build_bvh(d->dyn_vertices, d->dyn_triangles, nd, ns);
+    sc->bvh_depth_static = bs.depth;
+    sc->bvh_depth_dyn = bd.depth;
+    if (bs.depth >= kStackDepth || bd.depth >= kStackDepth) {
+        delete sc;
+        return fail(RP_ERR_UNSUPPORTED, "BVH deeper than the traversal stack");
+    }
+    // triangles by id: three vertices, and in their .w slots the unit normal
+    // computed in double precision
+    std::vector<float4> st(3 * (size_t)ns), dt(3 * (size_t)nd);
+    auto fill = [](const float *verts, const uint32_t *tri, float4 *out) {
+        const float *p[3] = {verts + 3 * tri[0], verts + 3 * tri[1], verts + 3 * tri[2]};
+        double e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = (double)p[1][a] - p[0][a];
+            e2[a] = (double)p[2][a] - p[0][a];
+        }
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                       e1[0] * e2[1] - e1[1] * e2[0]};
+        double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int a = 0; a < 3; ++a) n[a] = l > 0.0 ? n[a] / l : 0.0;
+        for (int k = 0; k < 3; ++k) out[k] = make_float4(p[k][0], p[k][1], p[k][2], (float)n[k]);
+    };
+    for (int i = 0; i < ns; ++i) fill(d->static_vertices, d->static_triangles + 3 * i, &st[3 * (size_t)i]);
+    for (int i = 0; i < nd; ++i) fill(d->dyn_vertices, d->dyn_triangles + 3 * i, &dt[3 * (size_t)i]);
+    auto area = [](const float4 *t) {
+        double e1[3] = {(double)t[1].x - t[0].x, (double)t[1].y - t[0].y, (double)t[1].z - t[0].z};
+        double e2[3] = {(double)t[2].x - t[0].x, (double)t[2].y - t[0].y, (double)t[2].z - t[0].z};
+        double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                       e1[0] * e2[1] - e1[1] * e2[0]};
+        return 0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    };
+    // area CDFs: p(x_D) = 1 / A_dyn and p(x_L) = 1 / A_emit
+    std::vector<float> dcdf(nd);
+    double acc = 0.0;
+    std::vector<double> dacc(nd);
+    for (int i = 0; i < nd; ++i) { acc += area(&dt[3 * (size_t)i]); dacc[i] = acc; }
+    const double dyn_area = acc;
+    for (int i = 0; i < nd; ++i) dcdf[i] = (float)(dacc[i] / dyn_area);
+    dcdf[nd - 1] = 1.0f;
+    std::vector<int> eids;
+    std::vector<double> eacc;
+    acc = 0.0;
+    for (int i = 0; i < ns; ++i) {
+        const float *m = d->materials + 12 * d->static_material[i];
+        if (m[8] == 0.f && m[9] == 0.f && m[10] == 0.f) continue;
+        acc += area(&st[3 * (size_t)i]);
+        eids.push_back(i);
+        eacc.push_back(acc);
+    }
+    if (eids.empty() || !(acc > 0.0) || !(dyn_area > 0.0)) {
+        delete sc;
+        return fail(RP_ERR_INVALID_ARG, "scene needs an emitter and a dynamic object of non-zero area");
+    }
+    std::vector<float> ecdf(eids.size());
+    for (size_t i = 0; i < eids.size(); ++i) ecdf[i] = (float)(eacc[i] / acc);
+    ecdf.back() = 1.0f;
+
+    std::vector<uint32_t> smat(d->static_material, d->static_material + ns);
+    std::vector<float> mats(d->materials, d->materials + 12 * (size_t)d->n_materials);
+    rp_status s = RP_OK;
+    float4 *p4;
+    float *pf;
+    uint32_t *pu;
+    int *pi;
+#define UP(vec, ptr, dst)                         \
+    if ((s = upload(vec, &ptr)) != RP_OK) {       \
+        delete sc;                                \
+        return s;                                 \
+    }                                             \
+    keep(ptr);                                    \
+    dst = ptr;
+    UP(bs.nodes, p4, S.stat.nodes);
+    UP(bs.tris, p4, S.stat.tris);
+    UP(bd.nodes, p4, S.dyn.nodes);
+    UP(bd.tris, p4, S.dyn.tris);
+    UP(st, p4, S.stat_tri);
+    UP(dt, p4, S.dyn_tri);
+    UP(smat, pu, S.stat_mat);
+    UP(mats, pf, S.mats);
+    UP(dcdf, pf, S.dyn_cdf);
+    UP(ecdf, pf, S.emit_cdf);
+    UP(eids, pi, S.emit_ids);
+#undef UP
+    S.stat.n_nodes = (int)(bs.nodes.size() / 4);
+    S.stat.n_tris = ns;
+    S.dyn.n_nodes = (int)(bd.nodes.size() / 4);
+    S.dyn.n_tris = nd;
+    S.n_static = ns;
+    S.n_dyn = nd;
+    S.n_emit = (int)eids.size();
+    S.n_mats = (int)d->n_materials;
+    S.dyn_area = (float)dyn_area;
+    S.emit_area = (float)acc;
+    // camera basis in double, stored as float
+    const float *c = d->camera;
+    double pos[3] = {c[0], c[1], c[2]}, look[3] = {c[3], c[4], c[5]}, up[3] = {c[6], c[7], c[8]};
+    double f[3] = {look[0] - pos[0], look[1] - pos[1], look[2] - pos[2]};
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (double &v : f) v /= fl;
+    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(fl > 0.0) || !(rl > 0.0) || !(c[9] > 0.f && c[9] < 180.f)) {
+        delete sc;
+        return fail(RP_ERR_INVALID_ARG, "degenerate camera");
+    }
+    for (double &v : r) v /= rl;
+    double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    S.cam_pos = make_float3((float)pos[0], (float)pos[1], (float)pos[2]);
+    S.cam_fwd = make_float3((float)f[0], (float)f[1], (float)f[2]);
+    S.cam_right = make_float3((float)r[0], (float)r[1], (float)r[2]);
+    S.cam_up = make_float3((float)u[0], (float)u[1], (float)u[2]);
+    double hh = std::tan(0.5 * (double)c[9] * 3.14159265358979323846 / 180.0);
+    double hw = hh * d->width / d->height;
+    S.hh = (float)hh;
+    S.hw = (float)hw;
+    S.pix_area = (float)((2.0 * hw / d->width) * (2.0 * hh / d->height));
+    S.film_area = (float)(4.0 * hw * hh);
+    S.W = (int)d->width;
+    S.H = (int)d->height;
+    S.max_depth = (int)d->max_depth;
+    S.alpha_min = d->alpha_min;
+    S.d_min = d->d_min;
+    S.jac_max = d->jacobian_max;
+    S.eps = 1e-5f;
+    cudaError_t e = cudaMalloc((void **)&sc->d_stats, sizeof(unsigned long long) * ST_COUNT);
+    if (e != cudaSuccess) {
+        delete sc;
+        return cuda_fail(e, "cudaMalloc stats");
+    }
+    cudaMemset(sc->d_stats, 0, sizeof(unsigned long long) * ST_COUNT);
+    *out = sc;
+    return RP_OK;
+}
+
+extern "C" void rp_scene_destroy(rp_scene *scene) { delete scene; }
+
+static void invert_rigid(const float *M, float *Mi) {
+    // inverse of [R | t] is [R^T | -R^T t], in double
+    double R[9], t[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) R[3 * i + j] = M[4 * i + j];
+        t[i] = M[4 * i + 3];
+    }
+    for (int i = 0; i < 3; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            Mi[4 * i + j] = (float)R[3 * j + i];
+            acc += R[3 * j + i] * t[j];
+        }
+        Mi[4 * i + 3] = (float)(-acc);
+    }
+}
+
+static bool rigid(const float *M) {
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(M[i])) return false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += (double)M[4 * i + k] * M[4 * j + k];
+            if (std::fabs(acc - (i == j ? 1.0 : 0.0)) > 1e-4) return false;
+        }
+    double det = (double)M[0] * (M[5] * M[10] - M[6] * M[9]) -
+                 (double)M[1] * (M[4] * M[10] - M[6] * M[8]) +
+                 (double)M[2] * (M[4] * M[9] - M[5] * M[8]);
+    return det > 0.0;
+}
+
+static rp_status fill_edit(const rp_edit_desc *d, DevEdit &E) {
+    if (!rigid(d->M1) || !rigid(d->M2))
+        return fail(RP_ERR_UNSUPPORTED, "edit transforms must be rigid (rotation + translation)");
+    if (!material_ok(d->mat1) || !material_ok(d->mat2))
+        return fail(RP_ERR_INVALID_ARG, "invalid edit material");
+    for (int i = 8; i < 11; ++i)
+        if (d->mat1[i] != 0.f || d->mat2[i] != 0.f)
+            return fail(RP_ERR_UNSUPPORTED, "the edited object may not be emissive");
+    std::memset(&E, 0, sizeof E);
+    std::memcpy(E.M[1], d->M1, sizeof(float) * 12);
+    std::memcpy(E.M[2], d->M2, sizeof(float) * 12);
+    invert_rigid(d->M1, E.Minv[1]);
+    invert_rigid(d->M2, E.Minv[2]);
+    std::memcpy(E.mat[1], d->mat1, sizeof(float) * 12);
+    std::memcpy(E.mat[2], d->mat2, sizeof(float) * 12);
+    E.motion = std::memcmp(d->M1, d->M2, sizeof(float) * 12) != 0;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out) {
+    if (!scene || !desc || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    rp_edit_handle *e = new rp_edit_s();
+    rp_status s = fill_edit(desc, e->E);
+    if (s != RP_OK) {
+        delete e;
+        return s;
+    }
+    *out = e;
+    return RP_OK;
+}
+
+extern "C" void rp_edit_destroy(rp_edit_handle *edit) { delete edit; }
+
+static LaunchArgs base_args(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
+                            uint32_t mask) {
+    LaunchArgs a{};
+    a.S = sc->S;
+    a.E = E;
+    a.seed = seed;
+    a.invN = (float)(1.0 / ((double)spp * sc->S.W * sc->S.H));
+    a.tech_mask = (int)mask;
+    a.stats = sc->stats_on ? sc->d_stats : nullptr;
+    return a;
+}
+
+static rp_status check_render(rp_scene *sc, uint32_t spp, uint32_t mask) {
+    if (!sc) return fail(RP_ERR_INVALID_ARG, "null scene");
+    if (spp == 0) return fail(RP_ERR_INVALID_ARG, "spp must be positive");
+    if ((uint64_t)spp * sc->S.W * sc->S.H > 0xffffffffull)
+        return fail(RP_ERR_INVALID_ARG, "spp * width * height must fit in 32 bits");
+    if (mask == 0 || (mask & ~RP_TECH_ALL)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
+    return RP_OK;
+}
+
+static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
+                             uint32_t mask, double *d_out, cudaStream_t st) {
+    LaunchArgs a = base_args(sc, E, spp, seed, mask);
+    a.img = d_out;
+    a.root_begin = 0;
+    a.root_end = spp * (uint32_t)(sc->S.W * sc->S.H);
+    if (sc->stats_on)
+        RP_CUDA(cudaMemsetAsync(sc->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, st), "memset");
+    const int techs[4] = {1, 2, 3, 7};
+    for (int g = 1; g <= 2; ++g)
+        for (int t = 0; t < 4; ++t) {
+            if (!(mask & (1u << t))) continue;
+            a.frame = g;
+            RP_CUDA(launch_residual(techs[t], a, st), "residual launch");
+        }
+    sc->last_stream = st;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_render_residual(rp_scene *scene, const rp_edit_handle *edit, uint32_t spp,
+                                        uint64_t seed, uint32_t tech_mask, double *d_out,
+                                        void *stream) {
+    if (rp_status s = check_render(scene, spp, tech_mask)) return s;
+    if (!edit || !d_out) return fail(RP_ERR_INVALID_ARG, "null edit or image");
+    return render_into(scene, edit->E, spp, seed, tech_mask, d_out, (cudaStream_t)stream);
+}
+
+static rp_status ensure_scratch(rp_scene *sc) {
+    if (sc->d_scratch) return RP_OK;
+    size_t n = (size_t)sc->S.W * sc->S.H * 3;
+    cudaError_t e = cudaMalloc((void **)&sc->d_scratch, n * sizeof(double));
+    if (e == cudaErrorMemoryAllocation) return fail(RP_ERR_OOM, "scratch image allocation failed");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc scratch");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_render_residual_f32(rp_scene *scene, const rp_edit_handle *edit,
+                                            uint32_t spp, uint64_t seed, uint32_t tech_mask,
+                                            float *d_out, void *stream) {
+    if (rp_status s = check_render(scene, spp, tech_mask)) return s;
+    if (!edit || !d_out) return fail(RP_ERR_INVALID_ARG, "null edit or image");
+    if (rp_status s = ensure_scratch(scene)) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = (size_t)scene->S.W * scene->S.H * 3;
+    RP_CUDA(cudaMemsetAsync(scene->d_scratch, 0, n * sizeof(double), st), "memset scratch");
+    if (rp_status s = render_into(scene, edit->E, spp, seed, tech_mask, scene->d_scratch, st))
+        return s;
+    RP_CUDA(launch_add_f64_to_f32(scene->d_scratch, d_out, n, st), "resolve launch");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_render_residual_host(rp_scene *scene, const rp_edit_desc *edit,
+                                             uint32_t spp, uint64_t seed, uint32_t tech_mask,
+                                             double *host_out, void *stream) {
+    if (rp_status s = check_render(scene, spp, tech_mask)) return s;
+    if (!edit || !host_out) return fail(RP_ERR_INVALID_ARG, "null edit or image");
+    DevEdit E;
+    if (rp_status s = fill_edit(edit, E)) return s;
+    if (rp_status s = ensure_scratch(scene)) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = (size_t)scene->S.W * scene->S.H * 3;
+    RP_CUDA(cudaMemsetAsync(scene->d_scratch, 0, n * sizeof(double), st), "memset scratch");
+    if (rp_status s = render_into(scene, E, spp, seed, tech_mask, scene->d_scratch, st)) return s;
+    RP_CUDA(cudaMemcpyAsync(host_out, scene->d_scratch, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            st),
+            "copy image to host");
+    RP_CUDA(cudaStreamSynchronize(st), "render");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_render_primal(rp_scene *scene, const rp_edit_handle *edit, int frame,
+                                      uint32_t spp, uint64_t seed, double *d_out, void *stream) {
+    if (rp_status s = check_render(scene, spp, RP_TECH_ALL)) return s;
+    if (!edit || !d_out) return fail(RP_ERR_INVALID_ARG, "null edit or image");
+    if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
+    cudaStream_t st = (cudaStream_t)stream;
+    LaunchArgs a = base_args(scene, edit->E, spp, seed, RP_TECH_ALL);
+    a.img = d_out;
+    a.frame = frame;
+    a.root_begin = 0;
+    a.root_end = spp * (uint32_t)(scene->S.W * scene->S.H);
+    if (scene->stats_on)
+        RP_CUDA(cudaMemsetAsync(scene->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, st),
+                "memset");
+    RP_CUDA(launch_primal(a, st), "primal launch");
+    scene->last_stream = st;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_dump_samples(rp_scene *scene, const rp_edit_handle *edit, int tech,
+                                     int frame, uint32_t spp, uint64_t seed, uint32_t root_begin,
+                                     uint32_t root_end, uint32_t tech_mask, rp_record *d_records,
+                                     uint64_t capacity, unsigned long long *d_count, void *stream) {
+    if (rp_status s = check_render(scene, spp, tech_mask)) return s;
+    if (!edit || !d_count || (!d_records && capacity)) return fail(RP_ERR_INVALID_ARG, "null buffer");
+    if (tech != 1 && tech != 2 && tech != 3 && tech != 7)
+        return fail(RP_ERR_INVALID_ARG, "tech must be 1, 2, 3 or 7");
+    if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
+    if (root_end < root_begin || root_end > spp * (uint32_t)(scene->S.W * scene->S.H))
+        return fail(RP_ERR_INVALID_ARG, "root range out of bounds");
+    static_assert(sizeof(rp_record) == sizeof(Record), "record layout");
+    cudaStream_t st = (cudaStream_t)stream;
+    RP_CUDA(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st), "memset count");
+    LaunchArgs a = base_args(scene, edit->E, spp, seed, tech_mask);
+    a.frame = frame;
+    a.root_begin = root_begin;
+    a.root_end = root_end;
+    a.rec = reinterpret_cast<Record *>(d_records);
+    a.rec_cap = capacity;
+    a.rec_count = d_count;
+    RP_CUDA(launch_residual(tech, a, st), "dump launch");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edit, int frame,
+                                      uint32_t n, const float *d_origins, const float *d_dirs,
+                                      float *d_t, int32_t *d_prim, float *d_b1, float *d_b2,
+                                      void *stream) {
+    if (!scene || !edit) return fail(RP_ERR_INVALID_ARG, "null scene or edit");
+    if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
+    if (n && (!d_origins || !d_dirs || !d_t || !d_prim || !d_b1 || !d_b2))
+        return fail(RP_ERR_INVALID_ARG, "null ray buffer");
+    RP_CUDA(launch_trace(scene->S, edit->E, frame, n, d_origins, d_dirs, d_t, d_prim, d_b1, d_b2,
+                         (cudaStream_t)stream),
+            "trace launch");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_philox(uint32_t n, const uint32_t *d_counters, const uint32_t *d_keys,
+                               uint32_t *d_out, void *stream) {
+    if (rp_status s = need_device()) return s;
+    if (n && (!d_counters || !d_keys || !d_out)) return fail(RP_ERR_INVALID_ARG, "null buffer");
+    RP_CUDA(launch_philox(n, d_counters, d_keys, d_out, (cudaStream_t)stream), "philox launch");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_enable_stats(rp_scene *scene, int on) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    scene->stats_on = on != 0;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_get_stats(rp_scene *scene, rp_stats *out) {
+    if (!scene || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
+    unsigned long long h[ST_COUNT];
+    RP_CUDA(cudaStreamSynchronize(scene->last_stream), "sync");
+    RP_CUDA(cudaMemcpy(h, scene->d_stats, sizeof h, cudaMemcpyDeviceToHost), "stats copy");
+    out->roots = h[ST_ROOTS];
+    out->paths = h[ST_PATHS];
+    out->rays_closest = h[ST_RAYS_CLOSEST];
+    out->rays_shadow = h[ST_RAYS_SHADOW];
+    out->nodes_visited = h[ST_NODES];
+    out->tris_tested = h[ST_TRIS];
+    out->accepted = h[ST_ACCEPTED];
+    out->rejected = h[ST_REJECTED];
+    return RP_OK;
+}

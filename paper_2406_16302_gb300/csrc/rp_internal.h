@@ -1,0 +1,96 @@
+// Internal layout of scenes and edits on the device, shared by the host
+// library code and the kernels (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rp {
+
+constexpr int kMaxDepth = 10;          // maximum path edges accepted by the API
+constexpr int kMaxVerts = kMaxDepth + 2;
+constexpr int kStackDepth = 40;        // traversal stack entries per thread
+constexpr int kBvhMaxDepth = 38;       // the builder never exceeds this depth
+constexpr int kBlock = 128;            // threads per block of the path kernels
+
+// BVH node: both children's boxes, 64 bytes.
+//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   d = (child0, child1, count0, count1) as int; child >= 0 is an inner
+//       node, child < 0 a leaf whose first triangle is ~child.
+// Leaf triangles: 3 float4 (v0, v1, v2); v0.w holds the global triangle id.
+struct DevBVH {
+    const float4 *nodes;
+    const float4 *tris;
+    int n_nodes;
+    int n_tris;
+};
+
+struct DevScene {
+    DevBVH stat, dyn;
+    const float4 *stat_tri;     // [n_static][3] world vertices by triangle id; .w = unit normal
+    const float4 *dyn_tri;      // [n_dyn][3] object-space vertices by triangle id; .w = unit normal
+    const uint32_t *stat_mat;   // [n_static] material index
+    const float *mats;          // [n_mats][12]
+    const float *dyn_cdf;       // [n_dyn] area CDF of the dynamic object
+    const float *emit_cdf;      // [n_emit] area CDF of the emitters
+    const int *emit_ids;        // [n_emit] static triangle ids
+    int n_static, n_dyn, n_emit, n_mats;
+    float dyn_area, emit_area;
+    float3 cam_pos, cam_fwd, cam_right, cam_up;
+    float hw, hh, pix_area, film_area;
+    int W, H;
+    int max_depth;
+    float alpha_min, d_min, jac_max, eps;
+};
+
+// Per-frame data of an edit; index 1 = original frame, 2 = edited frame.
+struct DevEdit {
+    float M[3][12];             // object -> world (row-major 3x4)
+    float Minv[3][12];          // world -> object
+    float mat[3][12];           // the dynamic object's material
+    int motion;                 // M1 != M2
+};
+
+struct Record {
+    uint32_t root;
+    int32_t tech, frame;
+    int32_t sa, sb;
+    int32_t pix_a, pix_b;
+    float va[3], vb[3];
+    int32_t status;
+    float Pg, Py, J;
+};
+
+enum StatIndex {
+    ST_ROOTS = 0, ST_PATHS, ST_RAYS_CLOSEST, ST_RAYS_SHADOW, ST_NODES, ST_TRIS,
+    ST_ACCEPTED, ST_REJECTED, ST_COUNT
+};
+
+struct LaunchArgs {
+    DevScene S;
+    DevEdit E;
+    int frame;
+    uint32_t root_begin, root_end;
+    uint64_t seed;
+    float invN;                 // 1 / (spp * W * H)
+    int tech_mask;
+    double *img;                // accumulation image or null
+    Record *rec;                // records or null
+    unsigned long long rec_cap;
+    unsigned long long *rec_count;
+    unsigned long long *stats;  // ST_COUNT counters or null
+};
+
+// launchers implemented in the .cu files
+cudaError_t launch_residual(int tech, const LaunchArgs &a, cudaStream_t s);
+cudaError_t launch_primal(const LaunchArgs &a, cudaStream_t s);
+cudaError_t launch_trace(const DevScene &S, const DevEdit &E, int frame, uint32_t n,
+                         const float *o, const float *d, float *t, int32_t *prim, float *b1,
+                         float *b2, cudaStream_t s);
+cudaError_t launch_philox(uint32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                          cudaStream_t s);
+cudaError_t launch_add_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t s);
+
+}  // namespace rp

@@ -1,0 +1,287 @@
+"""Python binding of librp (include/rp.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; all computation
+runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors,
+passed by ``data_ptr()``; streams are torch streams.  If ``librp.so`` has not
+been built, or no CUDA device is present, calls raise: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librp.so")
+
+RP_OK = 0
+RP_TECH_ALL = 15
+STATUS = {0: "RP_OK", 1: "RP_ERR_INVALID_ARG", 2: "RP_ERR_OOM", 3: "RP_ERR_CUDA",
+          4: "RP_ERR_TIMEOUT", 5: "RP_ERR_UNSUPPORTED"}
+
+
+class RPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rp_scene_desc(C.Structure):
+    _fields_ = [("static_vertices", C.c_void_p), ("n_static_vertices", C.c_uint32),
+                ("static_triangles", C.c_void_p), ("static_material", C.c_void_p),
+                ("n_static_triangles", C.c_uint32),
+                ("dyn_vertices", C.c_void_p), ("n_dyn_vertices", C.c_uint32),
+                ("dyn_triangles", C.c_void_p), ("n_dyn_triangles", C.c_uint32),
+                ("materials", C.c_void_p), ("n_materials", C.c_uint32),
+                ("camera", C.c_float * 10), ("width", C.c_uint32), ("height", C.c_uint32),
+                ("max_depth", C.c_uint32), ("alpha_min", C.c_float), ("d_min", C.c_float),
+                ("jacobian_max", C.c_float)]
+
+
+class rp_edit_desc(C.Structure):
+    _fields_ = [("M1", C.c_float * 12), ("M2", C.c_float * 12),
+                ("mat1", C.c_float * 12), ("mat2", C.c_float * 12)]
+
+
+class rp_stats(C.Structure):
+    _fields_ = [(n, C.c_ulonglong) for n in ("roots", "paths", "rays_closest", "rays_shadow",
+                                              "nodes_visited", "tris_tested", "accepted",
+                                              "rejected")]
+
+
+RECORD_DTYPE = np.dtype([
+    ("root", "<u4"), ("tech", "<i4"), ("frame", "<i4"), ("sa", "<i4"), ("sb", "<i4"),
+    ("pix_a", "<i4"), ("pix_b", "<i4"), ("va", "<f4", 3), ("vb", "<f4", 3),
+    ("status", "<i4"), ("Pg", "<f4"), ("Py", "<f4"), ("J", "<f4")])
+
+# every symbol the header declares
+EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
+           "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_host",
+           "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
+           "rp_enable_stats", "rp_get_stats", "rp_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Load librp.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2406_16302_gb300.build` (there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    P, U32, U64, I = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+    sig = {
+        "rp_scene_create": (I, [P, P]),
+        "rp_scene_destroy": (None, [P]),
+        "rp_edit": (I, [P, P, P]),
+        "rp_edit_destroy": (None, [P]),
+        "rp_render_residual": (I, [P, P, U32, U64, U32, P, P]),
+        "rp_render_residual_f32": (I, [P, P, U32, U64, U32, P, P]),
+        "rp_render_residual_host": (I, [P, P, U32, U64, U32, P, P]),
+        "rp_render_primal": (I, [P, P, I, U32, U64, P, P]),
+        "rp_dump_samples": (I, [P, P, I, I, U32, U64, U32, U32, U32, P, U64, P, P]),
+        "rp_trace_closest": (I, [P, P, I, U32, P, P, P, P, P, P, P]),
+        "rp_philox": (I, [U32, P, P, P, P]),
+        "rp_enable_stats": (I, [P, I]),
+        "rp_get_stats": (I, [P, P]),
+        "rp_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != RP_OK:
+        raise RPError(status, lib().rp_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def edit_desc(edit) -> rp_edit_desc:
+    d = rp_edit_desc()
+    d.M1[:] = [float(v) for v in np.asarray(edit.M1, np.float32).ravel()]
+    d.M2[:] = [float(v) for v in np.asarray(edit.M2, np.float32).ravel()]
+    d.mat1[:] = [float(v) for v in np.asarray(edit.mat1, np.float32).ravel()]
+    d.mat2[:] = [float(v) for v in np.asarray(edit.mat2, np.float32).ravel()]
+    return d
+
+
+class Scene:
+    """rp_scene_create / rp_scene_destroy around a scenes.Scene."""
+
+    def __init__(self, scene):
+        self.src = scene
+        arrs = [np.ascontiguousarray(scene.static_vertices, np.float32),
+                np.ascontiguousarray(scene.static_triangles, np.uint32),
+                np.ascontiguousarray(scene.static_material, np.uint32),
+                np.ascontiguousarray(scene.dyn_vertices, np.float32),
+                np.ascontiguousarray(scene.dyn_triangles, np.uint32),
+                np.ascontiguousarray(scene.materials, np.float32)]
+        sv, st, sm, dv, dt, mats = arrs
+        d = rp_scene_desc()
+        d.static_vertices = sv.ctypes.data
+        d.n_static_vertices = len(sv)
+        d.static_triangles = st.ctypes.data
+        d.static_material = sm.ctypes.data
+        d.n_static_triangles = len(st)
+        d.dyn_vertices = dv.ctypes.data
+        d.n_dyn_vertices = len(dv)
+        d.dyn_triangles = dt.ctypes.data
+        d.n_dyn_triangles = len(dt)
+        d.materials = mats.ctypes.data
+        d.n_materials = len(mats)
+        d.camera[:] = [float(v) for v in scene.camera.as_array()]
+        d.width, d.height = scene.camera.width, scene.camera.height
+        d.max_depth = scene.max_depth
+        d.alpha_min, d.d_min, d.jacobian_max = scene.alpha_min, scene.d_min, scene.jacobian_max
+        h = C.c_void_p()
+        _check(lib().rp_scene_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.width, self.height = scene.camera.width, scene.camera.height
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rp_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.height, self.width, 3)
+
+    def n_roots(self, spp):
+        return spp * self.width * self.height
+
+
+class Edit:
+    """rp_edit / rp_edit_destroy around a scenes.Edit."""
+
+    def __init__(self, scene: Scene, edit):
+        self.desc = edit_desc(edit)
+        h = C.c_void_p()
+        _check(lib().rp_edit(scene.h, C.byref(self.desc), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rp_edit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rp_render_residual(scene: Scene, edit: Edit, spp, seed, out, tech_mask=RP_TECH_ALL,
+                       stream=None):
+    _check(lib().rp_render_residual(scene.h, edit.h, spp, seed, tech_mask, _ptr(out),
+                                    _stream(stream)))
+
+
+def rp_render_residual_f32(scene: Scene, edit: Edit, spp, seed, out, tech_mask=RP_TECH_ALL,
+                           stream=None):
+    _check(lib().rp_render_residual_f32(scene.h, edit.h, spp, seed, tech_mask, _ptr(out),
+                                        _stream(stream)))
+
+
+def rp_render_residual_host(scene: Scene, edit, spp, seed, host_out: np.ndarray,
+                            tech_mask=RP_TECH_ALL, stream=None):
+    assert host_out.dtype == np.float64 and host_out.flags.c_contiguous
+    d = edit_desc(edit)
+    _check(lib().rp_render_residual_host(scene.h, C.byref(d), spp, seed, tech_mask,
+                                         host_out.ctypes.data_as(C.c_void_p), _stream(stream)))
+
+
+def rp_render_primal(scene: Scene, edit: Edit, frame, spp, seed, out, stream=None):
+    _check(lib().rp_render_primal(scene.h, edit.h, frame, spp, seed, _ptr(out), _stream(stream)))
+
+
+def rp_dump_samples(scene: Scene, edit: Edit, tech, frame, spp, seed, root_begin, root_end,
+                    records, count, tech_mask=RP_TECH_ALL, stream=None):
+    cap = 0 if records is None else records.numel() * records.element_size() // RECORD_DTYPE.itemsize
+    _check(lib().rp_dump_samples(scene.h, edit.h, tech, frame, spp, seed, root_begin, root_end,
+                                 tech_mask, _ptr(records), cap, _ptr(count), _stream(stream)))
+
+
+def rp_trace_closest(scene: Scene, edit: Edit, frame, origins, dirs, t, prim, b1, b2,
+                     stream=None):
+    n = origins.shape[0]
+    _check(lib().rp_trace_closest(scene.h, edit.h, frame, n, _ptr(origins), _ptr(dirs), _ptr(t),
+                                  _ptr(prim), _ptr(b1), _ptr(b2), _stream(stream)))
+
+
+def rp_philox(counters, keys, out, stream=None):
+    _check(lib().rp_philox(counters.shape[0], _ptr(counters), _ptr(keys), _ptr(out),
+                           _stream(stream)))
+
+
+def rp_enable_stats(scene: Scene, on=True):
+    _check(lib().rp_enable_stats(scene.h, 1 if on else 0))
+
+
+def rp_get_stats(scene: Scene) -> dict:
+    s = rp_stats()
+    _check(lib().rp_get_stats(scene.h, C.byref(s)))
+    return {n: int(getattr(s, n)) for n, _ in rp_stats._fields_}
+
+
+# ---------------------------------------------------------------------------
+# conveniences built only from the calls above
+# ---------------------------------------------------------------------------
+
+def render_residual(scene: Scene, edit: Edit, spp, seed, tech_mask=RP_TECH_ALL):
+    import torch
+    out = torch.zeros(scene.shape, dtype=torch.float64, device="cuda")
+    rp_render_residual(scene, edit, spp, seed, out, tech_mask)
+    return out
+
+
+def render_primal(scene: Scene, edit: Edit, frame, spp, seed):
+    import torch
+    out = torch.zeros(scene.shape, dtype=torch.float64, device="cuda")
+    rp_render_primal(scene, edit, frame, spp, seed, out)
+    return out
+
+
+def dump_samples(scene: Scene, edit: Edit, tech, frame, spp, seed, root_begin, root_end,
+                 tech_mask=RP_TECH_ALL, capacity=None):
+    """Records as a numpy structured array (RECORD_DTYPE)."""
+    import torch
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    if capacity is None:
+        rp_dump_samples(scene, edit, tech, frame, spp, seed, root_begin, root_end, None, count,
+                        tech_mask)
+        capacity = int(count.item())
+    nbytes = max(1, capacity) * RECORD_DTYPE.itemsize
+    buf = torch.zeros(nbytes // 4, dtype=torch.int32, device="cuda")
+    rp_dump_samples(scene, edit, tech, frame, spp, seed, root_begin, root_end, buf, count,
+                    tech_mask)
+    n = min(int(count.item()), capacity)
+    return buf.cpu().numpy().view(RECORD_DTYPE)[:n].copy()

@@ -1,0 +1,355 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerance: the library computes geometry and shading in FP32 and the oracle
+in FP64, from the same float32 scene data and the same Philox counters.  A
+sample matches when both splats land on the same pixels and each agrees
+within 1e-4 relative to the sample's magnitude; at least 99.9% of samples
+must match (a path can legitimately diverge when an FP32 ray grazes an edge
+or a pixel boundary).  Integer and index work (Philox, hit primitive ids) is
+compared exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2406_16302_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+MATCH_FRAC = 0.999          # over all paths of a case
+MATCH_FRAC_EACH = 0.995     # floor for each (technique, frame) subset
+
+
+class Tally:
+    def __init__(self):
+        self.good = 0
+        self.n = 0
+        self.worst = []
+
+    def add(self, frac, n, bad, label):
+        assert frac >= MATCH_FRAC_EACH, (label, frac, n, bad[:10])
+        self.good += round(frac * n)
+        self.n += n
+        self.worst += bad[:3]
+
+    def check(self, min_n=100):
+        assert self.n >= min_n, self.n
+        assert self.good / self.n >= MATCH_FRAC, (self.good / self.n, self.n, self.worst[:10])
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2406_16302_gb300 import build, rp as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def _compare(gpu, ora, rel=REL_TOL):
+    """Match records by (root, tech, frame, sa, sb); returns (fraction of
+    matching samples, number of samples, details)."""
+    def key(r):
+        return (int(r["root"]), int(r["tech"]), int(r["frame"]), int(r["sa"]), int(r["sb"]))
+    go = {key(r): r for r in gpu}
+    oo = {key(r): r for r in ora}
+    assert len(go) == len(gpu) and len(oo) == len(ora), "duplicate sample keys"
+    keys = set(go) | set(oo)
+    good = 0
+    bad = []
+    for k in keys:
+        g, o = go.get(k), oo.get(k)
+        if g is None or o is None:
+            bad.append((k, "missing on " + ("gpu" if g is None else "oracle")))
+            continue
+        scale = max(np.abs(o["va"]).max(), np.abs(o["vb"]).max(), 1e-300)
+        ok = (g["pix_a"] == o["pix_a"] and g["pix_b"] == o["pix_b"]
+              and np.all(np.abs(g["va"] - o["va"]) <= rel * scale)
+              and np.all(np.abs(g["vb"] - o["vb"]) <= rel * scale))
+        if ok:
+            good += 1
+        else:
+            bad.append((k, "value"))
+    n = max(len(keys), 1)
+    return good / n, len(keys), bad
+
+
+def _scene(builder, **kw):
+    scene, edit = getattr(S, builder)(**kw)
+    return scene, edit
+
+
+# --- random numbers and intersection --------------------------------------
+
+def test_philox_matches_known_answers_and_oracle(rp):
+    import torch
+    rows = [[int(w, 16) for w in l.split()] for l in open("tests/golden/philox4x32_10_kat.txt")
+            if l.strip() and not l.startswith("#")]
+    rng = np.random.RandomState(0)
+    ctr = np.concatenate([np.array([r[0:4] for r in rows], np.uint32),
+                          rng.randint(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)])
+    key = np.concatenate([np.array([r[4:6] for r in rows], np.uint32),
+                          rng.randint(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)])
+    d_c = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_k = torch.from_numpy(key.view(np.int32)).cuda()
+    d_o = torch.zeros_like(d_c)
+    rp.rp_philox(d_c, d_k, d_o)
+    out = d_o.cpu().numpy().view(np.uint32)
+    for i, r in enumerate(rows):
+        assert out[i].tolist() == r[6:10]
+    for i in range(len(rows), len(ctr), 97):
+        assert out[i].tolist() == O.philox4x32_10(ctr[i], key[i]).tolist()
+
+
+@pytest.mark.parametrize("builder,kw", [("cfg1_box_sphere", {}),
+                                        ("cfg2_box_blob", {"blob_level": 4})])
+def test_closest_hit_matches_oracle(rp, builder, kw):
+    import torch
+    scene, edit = _scene(builder, width=16, height=16, **kw)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    rng = np.random.RandomState(11)
+    n = 20000
+    o = rng.uniform(-0.95, 0.95, size=(n, 3)).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    for frame in (1, 2):
+        t = torch.zeros(n, device="cuda")
+        prim = torch.zeros(n, dtype=torch.int32, device="cuda")
+        b1 = torch.zeros(n, device="cuda")
+        b2 = torch.zeros(n, device="cuda")
+        rp.rp_trace_closest(sc, ed, frame, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(),
+                            t, prim, b1, b2)
+        tg, pg = t.cpu().numpy(), prim.cpu().numpy()
+        to, po, _, _ = ora.closest_hit(frame, o.astype(np.float64), d.astype(np.float64))
+        same = pg == po
+        assert same.mean() >= MATCH_FRAC, same.mean()
+        hit = same & (po >= 0)
+        # FP32 positions of order 1 carry an absolute error near 1e-7
+        assert np.all(np.abs(tg[hit] - to[hit]) <= 1e-5 * to[hit] + 2e-6)
+
+
+# --- per-sample parity ------------------------------------------------------
+
+PARITY_CASES = [
+    # (builder, kwargs, spp, roots per technique and frame)
+    ("cfg1_box_sphere", {}, 16, (0, 4096)),                         # motion, 64x64, D = 4
+    ("cfg1_box_sphere", {"max_depth": 6, "width": 33, "height": 17}, 3, (100, 1683)),  # ragged
+    ("cfg2_box_blob", {"width": 32, "height": 32, "blob_level": 3}, 4, (0, 2048)),  # material
+]
+
+
+@pytest.mark.parametrize("builder,kw,spp,rng_", PARITY_CASES)
+def test_per_sample_parity(rp, builder, kw, spp, rng_):
+    scene, edit = _scene(builder, **kw)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    r0, r1 = rng_
+    tally = Tally()
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            g = rp.dump_samples(sc, ed, tech, frame, spp, 1, r0, r1)
+            o = ora.dump(tech, frame, spp, 1, r0, r1)
+            tally.add(*_compare(g, o), (tech, frame))
+    tally.check(1000)
+
+
+def test_rotation_and_glossy_parity(rp):
+    """A rotating object over glossy walls exercises replay of GGX steps."""
+    scene, edit = S.cfg1_box_sphere(width=32, height=32, max_depth=6)
+    mats = scene.materials.copy()
+    mats[0] = S.material(S.GGX, alpha=0.4, f0=(0.6, 0.6, 0.6))
+    scene.materials = mats
+    edit.M2 = S.rotate_y_translate(25.0, edit.M1[:, 3].astype(np.float64) + np.array([0.05, 0.02, 0]))
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    tally = Tally()
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            g = rp.dump_samples(sc, ed, tech, frame, 8, 3, 0, 4096)
+            o = ora.dump(tech, frame, 8, 3, 0, 4096)
+            tally.add(*_compare(g, o), (tech, frame))
+    tally.check(1000)
+
+
+def test_replay_only_parity(rp):
+    """d_min larger than the scene disables reconnection: every walk vertex
+    of every mapped path is replayed (random-seed replay, Sec. 5)."""
+    scene, edit = S.cfg1_box_sphere(width=32, height=32, max_depth=6)
+    scene.d_min = 100.0
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    tally = Tally()
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            g = rp.dump_samples(sc, ed, tech, frame, 8, 5, 0, 4096)
+            o = ora.dump(tech, frame, 8, 5, 0, 4096)
+            tally.add(*_compare(g, o), (tech, frame))
+    tally.check(1000)
+
+
+def test_full_size_material_edit_sampled_roots(rp):
+    """The benchmark configuration (256x256, 64 spp, max depth 8, 20480-
+    triangle blob): roots sampled across the whole range, in the launch
+    configuration the benchmark uses."""
+    scene, edit = S.cfg2_box_blob()
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    N = sc.n_roots(64)
+    starts = np.linspace(0, N - 64, 12).astype(np.int64)
+    tally = Tally()
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            g_all, o_all = [], []
+            for s in starts:
+                g_all.append(rp.dump_samples(sc, ed, tech, frame, 64, 1, int(s), int(s) + 64))
+                o_all.append(ora.dump(tech, frame, 64, 1, int(s), int(s) + 64))
+            tally.add(*_compare(np.concatenate(g_all), np.concatenate(o_all)), (tech, frame))
+    tally.check(1000)
+
+
+def test_full_size_terrain_sampled_roots(rp):
+    """The scale configuration (1024x1024, 256 spp, ~1M triangles, 50k-
+    triangle rotating object): sampled roots near the ends of the 2^28 range."""
+    scene, edit = S.cfg3_terrain()
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    N = sc.n_roots(256)
+    good = n_all = 0
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            g = np.concatenate([rp.dump_samples(sc, ed, tech, frame, 256, 1, 0, 256),
+                                rp.dump_samples(sc, ed, tech, frame, 256, 1, N - 256, N)])
+            o = np.concatenate([ora.dump(tech, frame, 256, 1, 0, 256),
+                                ora.dump(tech, frame, 256, 1, N - 256, N)])
+            frac, n, bad = _compare(g, o)
+            good += n - len(bad)
+            n_all += n
+    # a few hundred paths: at most one marginal FP32 mismatch allowed
+    assert n_all > 100 and n_all - good <= max(1, int((1 - MATCH_FRAC) * n_all)), (good, n_all)
+
+
+# --- images ------------------------------------------------------------------
+
+def test_residual_image_matches_oracle(rp):
+    scene, edit = S.cfg1_box_sphere()
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    g = rp.render_residual(sc, ed, 16, 1).cpu().numpy()
+    o = O.Oracle(scene, edit).render_residual(16, 1)
+    scale = np.abs(o).max()
+    err = np.abs(g - o)
+    # pixels sum many samples; a marginal sample moves a pixel by far less
+    # than its own value
+    assert np.mean(err <= 1e-4 * scale) >= 0.999, np.sort(err.ravel())[-10:] / scale
+    assert err.max() <= 1e-2 * scale
+    assert abs(g.sum() - o.sum()) <= 1e-4 * np.abs(o).sum()
+
+
+def test_primal_image_matches_oracle(rp):
+    scene, edit = S.cfg1_box_sphere(width=32, height=32)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ora = O.Oracle(scene, edit)
+    for frame in (1, 2):
+        g = rp.render_primal(sc, ed, frame, 8, 4).cpu().numpy()
+        o = ora.render_primal(frame, 8, 4)
+        err = np.abs(g - o)
+        assert np.mean(err <= 1e-4 * np.abs(o).max()) >= 0.999
+        assert abs(g.sum() / o.sum() - 1) < 1e-4
+
+
+def test_residual_unbiased_against_correlated_pt_on_gpu(rp):
+    """Statistical check of the CUDA path on its own: residual estimate vs
+    correlated path tracing (same primary samples in both frames)."""
+    scene, edit = S.cfg1_box_sphere(width=16, height=16, max_depth=5)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    K = 32
+    res = np.array([rp.render_residual(sc, ed, 512, 1000 + i).cpu().numpy() for i in range(K)])
+    corr = np.array([(rp.render_primal(sc, ed, 2, 4096, 5000 + i)
+                      - rp.render_primal(sc, ed, 1, 4096, 5000 + i)).cpu().numpy()
+                     for i in range(K)])
+    sr, sc_ = res.reshape(K, -1).sum(1), corr.reshape(K, -1).sum(1)
+    z = (sr.mean() - sc_.mean()) / np.sqrt(sr.var(ddof=1) / K + sc_.var(ddof=1) / K)
+    assert abs(z) < 4.0, z
+    zp = (res.mean(0) - corr.mean(0)) / np.sqrt(res.var(0, ddof=1) / K + corr.var(0, ddof=1) / K + 1e-30)
+    assert np.sqrt((zp ** 2).mean()) < 1.4
+
+
+# --- entry points and edge cases ---------------------------------------------
+
+def test_identity_edit_is_exactly_zero_on_gpu(rp):
+    scene, edit = S.cfg2_box_blob(width=64, height=64, blob_level=3)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, S.identity_edit(edit))
+    img = rp.render_residual(sc, ed, 4, 9).cpu().numpy()
+    assert np.all(img == 0.0)
+
+
+def test_f32_and_host_entry_points_agree(rp):
+    import torch
+    scene, edit = S.cfg1_box_sphere(width=32, height=32)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    ref = rp.render_residual(sc, ed, 4, 2).cpu().numpy()
+    f32 = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+    rp.rp_render_residual_f32(sc, ed, 4, 2, f32)
+    host = np.zeros(sc.shape, dtype=np.float64)
+    rp.rp_render_residual_host(sc, edit, 4, 2, host)
+    tol = 1e-9 * np.abs(ref).max()
+    assert np.allclose(host, ref, rtol=1e-9, atol=tol)
+    assert np.allclose(f32.cpu().numpy(), ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
+def test_root_ranges_partition_the_image(rp):
+    """Rendering sub-ranges of roots (as ranks of a sharded run would) sums to
+    the full render."""
+    scene, edit = S.cfg1_box_sphere(width=16, height=16)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    full = rp.render_residual(sc, ed, 4, 3).cpu().numpy()
+    N = sc.n_roots(4)
+    parts = 0
+    for a, b in ((0, 333), (333, 1000), (1000, N)):
+        for tech in (1, 2, 3, 7):
+            for frame in (1, 2):
+                rec = rp.dump_samples(sc, ed, tech, frame, 4, 3, a, b)
+                parts += rec["va"].sum() + rec["vb"].sum()
+    assert abs(parts - full.sum()) <= 1e-4 * np.abs(full).sum()
+
+
+def test_invalid_arguments_are_rejected(rp):
+    import torch
+    scene, edit = S.cfg1_box_sphere(width=8, height=8)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    out = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(rp.RPError) as e:
+        rp.rp_render_residual(sc, ed, 0, 1, out)
+    assert e.value.status == 1
+    with pytest.raises(rp.RPError):
+        rp.rp_render_residual(sc, ed, 1, 1, out, tech_mask=0)
+    bad = S.cfg1_box_sphere(width=8, height=8)[1]
+    bad.M2 = bad.M2.copy()
+    bad.M2[0, 0] = 2.0                     # not rigid
+    with pytest.raises(rp.RPError) as e:
+        rp.Edit(sc, bad)
+    assert e.value.status == 5
+    s2, _ = S.cfg1_box_sphere(width=8, height=8)
+    s2.max_depth = 11
+    with pytest.raises(rp.RPError):
+        rp.Scene(s2)
+    s3, _ = S.cfg1_box_sphere(width=8, height=8)
+    s3.static_triangles = s3.static_triangles.copy()
+    s3.static_triangles[0, 0] = 10 ** 6
+    with pytest.raises(rp.RPError):
+        rp.Scene(s3)
