@@ -130,6 +130,28 @@ rp_status rp_render_residual(rp_scene *scene, const rp_edit_handle *edit, uint32
 rp_status rp_render_residual_f32(rp_scene *scene, const rp_edit_handle *edit, uint32_t spp,
                                  uint64_t seed, uint32_t tech_mask, float *d_out, void *stream);
 
+/* rp_render_residual_f32 without any device allocation.  The paper has no
+ * counterpart: this serves hosts that cannot let a library allocate device
+ * memory (they manage every byte through their own pool, run under a hard
+ * memory cap, or forbid allocation after start-up because cudaMalloc may
+ * synchronise the device).  Instead of a cudaMalloc'd scratch image the call
+ * uses a fixed FP64 array compiled into the library's device image, so every
+ * GPU that loads librp holds RP_NOALLOC_MAX_PIXELS * 3 doubles (24 MiB) until
+ * the process exits.  Same arguments, result and accumulation into d_out as
+ * rp_render_residual_f32.
+ *   - width * height above RP_NOALLOC_MAX_PIXELS: RP_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (once per device, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and clears it first: calls
+ *     that overlap on the GPU (other streams, other threads) race and give
+ *     wrong images.  Serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define RP_NOALLOC_MAX_PIXELS (1024u * 1024u)
+rp_status rp_render_residual_f32_noalloc(rp_scene *scene, const rp_edit_handle *edit,
+                                         uint32_t spp, uint64_t seed, uint32_t tech_mask,
+                                         float *d_out, void *stream);
+
 /* End-to-end convenience call with HOST buffers: uploads the edit, renders
  * the residual and copies it into host_out[height][width][3] (double,
  * overwritten, not accumulated).  Synchronous on `stream`. */

@@ -500,3 +500,29 @@ extern "C" rp_status rp_get_stats(rp_scene *scene, rp_stats *out) {
     out->rejected = h[ST_REJECTED];
     return RP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// helpers for entry points defined in other translation units
+// ---------------------------------------------------------------------------
+
+namespace rp {
+
+rp_status set_last_error(rp_status s, const char *msg) { return fail(s, msg); }
+
+rp_status scene_image_size(const rp_scene *scene, int *w, int *h) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    *w = scene->S.W;
+    *h = scene->S.H;
+    return RP_OK;
+}
+
+// validated residual render into a caller-supplied FP64 image (no allocation)
+rp_status render_residual_into(rp_scene *scene, const rp_edit_handle *edit, uint32_t spp,
+                               uint64_t seed, uint32_t tech_mask, double *d_img,
+                               cudaStream_t stream) {
+    if (rp_status s = check_render(scene, spp, tech_mask)) return s;
+    if (!edit || !d_img) return fail(RP_ERR_INVALID_ARG, "null edit or image");
+    return render_into(scene, edit->E, spp, seed, tech_mask, d_img, stream);
+}
+
+}  // namespace rp

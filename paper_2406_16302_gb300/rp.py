@@ -58,7 +58,8 @@ RECORD_DTYPE = np.dtype([
 
 # every symbol the header declares
 EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
-           "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_host",
+           "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_f32_noalloc",
+           "rp_render_residual_host",
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
            "rp_enable_stats", "rp_get_stats", "rp_last_error"]
 
@@ -82,6 +83,7 @@ def lib():
         "rp_edit_destroy": (None, [P]),
         "rp_render_residual": (I, [P, P, U32, U64, U32, P, P]),
         "rp_render_residual_f32": (I, [P, P, U32, U64, U32, P, P]),
+        "rp_render_residual_f32_noalloc": (I, [P, P, U32, U64, U32, P, P]),
         "rp_render_residual_host": (I, [P, P, U32, U64, U32, P, P]),
         "rp_render_primal": (I, [P, P, I, U32, U64, P, P]),
         "rp_dump_samples": (I, [P, P, I, I, U32, U64, U32, U32, U32, P, U64, P, P]),
@@ -209,6 +211,15 @@ def rp_render_residual_f32(scene: Scene, edit: Edit, spp, seed, out, tech_mask=R
                            stream=None):
     _check(lib().rp_render_residual_f32(scene.h, edit.h, spp, seed, tech_mask, _ptr(out),
                                         _stream(stream)))
+
+
+def rp_render_residual_f32_noalloc(scene: Scene, edit: Edit, spp, seed, out,
+                                   tech_mask=RP_TECH_ALL, stream=None):
+    """The float32 residual render with no device allocation (scratch lives in
+    a fixed array inside the library; width * height <= 1048576; calls that
+    overlap on the GPU race)."""
+    _check(lib().rp_render_residual_f32_noalloc(scene.h, edit.h, spp, seed, tech_mask, _ptr(out),
+                                                _stream(stream)))
 
 
 def rp_render_residual_host(scene: Scene, edit, spp, seed, host_out: np.ndarray,
