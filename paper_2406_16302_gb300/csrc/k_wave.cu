@@ -1,0 +1,597 @@
+// Wavefront execution of one wave of roots of one technique in one frame.
+//
+// Stage A (walks):   k_gen -> [k_trace_shadow -> k_start] ->
+//                    { k_trace_closest -> k_extend -> k_trace_shadow } x depth
+//   Rays live in SoA queues; kernels append with one atomic per coalesced
+//   group of threads.  Walk vertices are stored in per-root vertex slots,
+//   connection visibility in per-root bit masks.
+// Stage B (k_eval):  one thread per root enumerates the base paths of its
+//   technique from the slots and masks.  Without motion (material or
+//   identity edits) the mapping is the identity and the path is evaluated and
+//   splatted here with no ray at all; with motion every non-static path
+//   becomes a mapping task.
+// Stage C (k_map):   one thread per mapping task: object transform,
+//   reconnection or random replay in the other frame, two-way MIS, splat.
+//
+// The random numbers, walk termination rules and path enumeration are those
+// of the one-thread-per-root kernels (rp_device.cuh), so both modes produce
+// the same samples.
+#include <cooperative_groups.h>
+
+#include "chain_eval.cuh"
+#include "rp_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rp {
+
+namespace {
+
+enum { SIDE_ROOT = 0, SIDE_EYE = 1, SIDE_LIGHT = 2 };
+
+// one atomicAdd per coalesced group of appending threads
+__device__ __forceinline__ uint32_t append(unsigned int *counter) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    uint32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned int)g.size());
+    base = g.shfl(base, 0);
+    return base + g.thread_rank();
+}
+
+__device__ __forceinline__ void store_vtx(const WaveBuf &W, int slot, uint32_t r, const Vtx &v) {
+    const size_t i = (size_t)slot * W.R + r;
+    W.px[i] = v.p.x; W.py[i] = v.p.y; W.pz[i] = v.p.z;
+    W.nx[i] = v.n.x; W.ny[i] = v.n.y; W.nz[i] = v.n.z;
+    W.b1[i] = v.b1; W.b2[i] = v.b2;
+    W.prim[i] = v.prim;
+}
+
+__device__ __forceinline__ Vtx load_vtx(const Ctx &c, const WaveBuf &W, int slot, uint32_t r) {
+    const size_t i = (size_t)slot * W.R + r;
+    Vtx v;
+    v.p = f3(W.px[i], W.py[i], W.pz[i]);
+    v.n = f3(W.nx[i], W.ny[i], W.nz[i]);
+    v.b1 = W.b1[i];
+    v.b2 = W.b2[i];
+    v.prim = W.prim[i];
+    v.mat = v.prim < c.A.S.n_static ? (int)c.A.S.stat_mat[v.prim] : kMatDynamic;
+    return v;
+}
+
+__device__ __forceinline__ void push_closest(const LaunchArgs &A, int buf, int it, float3 o,
+                                             float3 d, int ex, uint32_t tag) {
+    const WaveBuf &W = A.W;
+    uint32_t i = append(W.counts + cnt_closest(it));
+    if (i >= W.qc) return;          // capacity is sized so that this cannot happen
+    W.c_o[buf][i] = o.x; W.c_o[buf][W.qc + i] = o.y; W.c_o[buf][2 * W.qc + i] = o.z;
+    W.c_d[buf][i] = d.x; W.c_d[buf][W.qc + i] = d.y; W.c_d[buf][2 * W.qc + i] = d.z;
+    W.c_ex[buf][i] = ex;
+    W.c_tag[buf][i] = tag;
+}
+
+// shadow ray over the open segment a -> b
+__device__ __forceinline__ void push_shadow(const LaunchArgs &A, int it, const Vtx &a, const Vtx &b,
+                                            uint32_t tag) {
+    const WaveBuf &W = A.W;
+    float3 e = b.p - a.p;
+    float dist = len3(e);
+    float3 d = e * (1.0f / dist);
+    uint32_t i = append(W.counts + cnt_shadow(it));
+    if (i >= W.qa) return;
+    W.a_o[i] = a.p.x; W.a_o[W.qa + i] = a.p.y; W.a_o[2 * W.qa + i] = a.p.z;
+    W.a_d[i] = d.x; W.a_d[W.qa + i] = d.y; W.a_d[2 * W.qa + i] = d.z;
+    W.a_tmax[i] = dist - A.S.eps;
+    W.a_ex0[i] = a.prim;
+    W.a_ex1[i] = b.prim;
+    W.a_tag[i] = tag;
+}
+
+__device__ __forceinline__ bool in_image_facing(const Ctx &c, const Vtx &z) {
+    float cc;
+    if (camera_project(c.A.S, z.p, cc) < 0) return false;
+    return faces(z, c.A.S.cam_pos);
+}
+
+// push the BSDF-sampled continuation of a walk at `at` (previous vertex
+// `prev`) with the numbers of (side, step)
+__device__ __forceinline__ void continue_walk(const Ctx &c, int buf, int it, uint32_t r,
+                                              const Vtx &prev, const Vtx &at, int tech, int rg,
+                                              int side, int step) {
+    const LaunchArgs &A = c.A;
+    float4 u = draw(A.seed, A.root_begin + r, tech, rg, side, step);
+    float3 wc = unit3(prev.p - at.p);
+    float3 wo;
+    Mat m = get_mat(c, A.frame, at.mat);
+    if (!bsdf_sample_walk(A.S, m, at.n, wc, u.x, u.y, wo)) return;
+    push_closest(A, buf, it, at.p, wo, at.prim, make_tag(r, side, step));
+}
+
+}  // namespace
+
+// --- stage A ---------------------------------------------------------------
+
+template <int T>
+__global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs A) {
+    const uint32_t n = A.root_end - A.root_begin;
+    const WaveBuf &W = A.W;
+    Ctx c(A, nullptr);
+    const int g = A.frame, D = A.S.max_depth;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint32_t root = A.root_begin + r;
+        W.len_eye[r] = 0;
+        W.len_light[r] = 0;
+        W.flags[r] = 0;
+        W.cam_ok[r] = 0u;
+        W.nee_ok[r] = 0u;
+        W.ghost_w[r] = 0u;
+        W.ghost_n[r] = 0u;
+        if (T == T_1 || T == T_2 || T == T_3) {
+            Vtx xD = sample_dynamic(c, g, draw(A.seed, root, T, g, SD_ROOT, 0));
+            store_vtx(W, 0, r, xD);
+            if (T == T_1) {
+                Vtx xL = sample_emitter(c, g, draw(A.seed, root, T_1, g, SD_NEE, 0));
+                store_vtx(W, 1, r, xL);
+                if (faces(xD, xL.p) && faces(xL, xD.p)) push_shadow(A, 0, xD, xL, make_tag(r, CK_NEE, 0));
+            } else if (T == T_2) {
+                if (!vtx_black(c, g, xD) && in_image_facing(c, xD))
+                    push_shadow(A, 0, xD, camera_vertex(c), make_tag(r, CK_CAMERA, 0));
+            } else {
+                if (D >= 4 && !vtx_black(c, g, xD)) {
+                    float4 u = draw(A.seed, root, T_3, g, SD_LIGHT, 1);
+                    float3 w = cosine_dir_walk(A.S, xD.n, u.x, u.y);
+                    if (dot3(xD.n, w) > 0.f) push_closest(A, 0, 0, xD.p, w, xD.prim, make_tag(r, SIDE_LIGHT, 1));
+                }
+            }
+        } else {
+            // path tracing: a stratified camera ray through pixel root mod (W H)
+            const int tech = A.residual ? T_7 : T_PT;
+            const int rg = A.residual ? g : 0;
+            const uint32_t npix = (uint32_t)(A.S.W * A.S.H);
+            const int pix = (int)(root % npix);
+            float4 u = draw(A.seed, root, tech, rg, SD_ROOT, 0);
+            float3 d = camera_dir(A.S, pix % A.S.W, pix / A.S.W, u.x, u.y);
+            push_closest(A, 0, 0, A.S.cam_pos, d, -1, make_tag(r, SIDE_ROOT, 0));
+        }
+    }
+}
+
+// techniques (1) and (2): start the walk of roots whose root connection is visible
+template <int T>
+__global__ void __launch_bounds__(256) k_start(const __grid_constant__ LaunchArgs A) {
+    const uint32_t n = A.root_end - A.root_begin;
+    const WaveBuf &W = A.W;
+    Ctx c(A, nullptr);
+    const int g = A.frame, D = A.S.max_depth;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        if (T == T_1) {
+            if (!(W.nee_ok[r] & 1u)) continue;
+            Vtx xD = load_vtx(c, W, 0, r);
+            if (vtx_black(c, g, xD)) continue;
+            W.flags[r] = RF_ROOT_OK;
+            if (in_image_facing(c, xD)) push_shadow(A, 1, xD, camera_vertex(c), make_tag(r, CK_CAMERA, 0));
+            if (D - 2 >= 1) {
+                Vtx xL = load_vtx(c, W, 1, r);
+                continue_walk(c, 0, 0, r, xL, xD, T_1, g, SD_EYE, 1);
+            }
+        } else {
+            if (!(W.cam_ok[r] & 1u)) continue;
+            W.flags[r] = RF_ROOT_OK;
+            if (D - 2 >= 1) {
+                Vtx xD = load_vtx(c, W, 0, r);
+                continue_walk(c, 0, 0, r, camera_vertex(c), xD, T_2, g, SD_LIGHT, 1);
+            }
+        }
+    }
+}
+
+// consume the hits of iteration it-1's closest rays; emit iteration it's rays
+template <int T>
+__global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchArgs A, int it) {
+    const WaveBuf &W = A.W;
+    const int in = (it - 1) & 1, out = it & 1;
+    const uint32_t n = min(W.counts[cnt_closest(it - 1)], W.qc);
+    Ctx c(A, nullptr);
+    const int g = A.frame, D = A.S.max_depth;
+    const int tech = (T == T_PT) ? (A.residual ? T_7 : T_PT) : T;
+    const int rg = (T == T_PT && !A.residual) ? 0 : g;
+    const bool ghosts = (T == T_PT) && A.residual && A.E.motion;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int prim = W.h_prim[i];
+        if (prim < 0) continue;
+        const uint32_t tag = W.c_tag[in][i];
+        const uint32_t r = tag_root(tag);
+        const int side = tag_side(tag), m = tag_step(tag);
+        const uint32_t root = A.root_begin + r;
+        const float3 d = f3(W.c_d[in][i], W.c_d[in][W.qc + i], W.c_d[in][2 * W.qc + i]);
+        Vtx v = make_vertex_at(c, g, prim, W.h_b1[i], W.h_b2[i],
+                               f3(W.h_p[i], W.h_p[W.qc + i], W.h_p[2 * W.qc + i]));
+        if (dot3(v.n, d) >= 0.f) continue;                     // back face
+        if (T == T_PT) {
+            // x_{j} with j = 1 (camera hit) or j = m + 1 (walk step m)
+            const int j = (side == SIDE_ROOT) ? 1 : m + 1;
+            store_vtx(W, j == 1 ? 0 : slot_light(D, m), r, v);
+            W.len_light[r] = j;
+            Vtx prev = (j == 1) ? camera_vertex(c) : load_vtx(c, W, j == 2 ? 0 : slot_light(D, j - 2), r);
+            if (ghosts) push_shadow(A, it + 1, prev, v, make_tag(r, CK_GHOST_WALK, j));
+            if (vtx_black(c, g, v)) continue;
+            Vtx L = sample_emitter(c, g, draw(A.seed, root, tech, rg, SD_NEE, j));
+            store_vtx(W, slot_nee(D, j), r, L);
+            if (faces(v, L.p) && faces(L, v.p)) {
+                push_shadow(A, it + 1, v, L, make_tag(r, CK_NEE, j));
+                if (ghosts) push_shadow(A, it + 1, v, L, make_tag(r, CK_GHOST_NEE, j));
+            }
+            if (j < D - 1) continue_walk(c, out, it, r, prev, v, tech, rg, SD_LIGHT, j);
+            continue;
+        }
+        if (vtx_black(c, g, v)) continue;
+        if (side == SIDE_EYE) {
+            // techniques (1) and (3): eye-side walk vertex z_m
+            store_vtx(W, slot_eye(D, m), r, v);
+            W.len_eye[r] = m;
+            if (in_image_facing(c, v)) push_shadow(A, it + 1, v, camera_vertex(c), make_tag(r, CK_CAMERA, m));
+            const int last = (T == T_1) ? D - 2 : D - 3;
+            if (m < last) {
+                Vtx prev = load_vtx(c, W, m == 1 ? 0 : slot_eye(D, m - 1), r);
+                continue_walk(c, out, it, r, prev, v, T, g, SD_EYE, m + 1);
+            }
+        } else {
+            // techniques (2) and (3): light-side walk vertex y_m with next-event estimation
+            store_vtx(W, slot_light(D, m), r, v);
+            W.len_light[r] = m;
+            Vtx L = sample_emitter(c, g, draw(A.seed, root, T, g, SD_NEE, m));
+            store_vtx(W, slot_nee(D, m), r, L);
+            if (faces(v, L.p) && faces(L, v.p)) push_shadow(A, it + 1, v, L, make_tag(r, CK_NEE, m));
+            const int last = (T == T_2) ? D - 2 : D - 3;
+            Vtx prev = load_vtx(c, W, m == 1 ? 0 : slot_light(D, m - 1), r);
+            if (m < last) continue_walk(c, out, it, r, prev, v, T, g, SD_LIGHT, m + 1);
+            if (T == T_3 && m == 1) {
+                // the eye side of (3) starts at x_D, conditioned on y_1
+                continue_walk(c, out, it, r, v, prev, T_3, g, SD_EYE, 1);
+            }
+        }
+    }
+}
+
+// closest hits of a queue
+__global__ void __launch_bounds__(kBlock) k_trace_closest(const __grid_constant__ LaunchArgs A, int it) {
+    __shared__ int s_stack[kStackDepth * kBlock];
+    Ctx c(A, s_stack + threadIdx.x);
+    const WaveBuf &W = A.W;
+    const int b = it & 1;
+    const uint32_t n = min(W.counts[cnt_closest(it)], W.qc);
+    const float inf = __int_as_float(0x7f800000);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float3 o = f3(W.c_o[b][i], W.c_o[b][W.qc + i], W.c_o[b][2 * W.qc + i]);
+        float3 d = f3(W.c_d[b][i], W.c_d[b][W.qc + i], W.c_d[b][2 * W.qc + i]);
+        Hit h;
+        ++c.cnt.rays_closest;
+        if (scene_trace(c, A.frame, o, d, A.S.eps, inf, W.c_ex[b][i], -1, false, false, h)) {
+            W.h_prim[i] = h.prim;
+            W.h_b1[i] = h.b1;
+            W.h_b2[i] = h.b2;
+            W.h_p[i] = h.p.x;
+            W.h_p[W.qc + i] = h.p.y;
+            W.h_p[2 * W.qc + i] = h.p.z;
+        } else {
+            W.h_prim[i] = -1;
+        }
+    }
+    if (A.stats) {
+        add_stat(A.stats, ST_RAYS_CLOSEST, c.cnt.rays_closest);
+        add_stat(A.stats, ST_NODES, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS, c.cnt.tris);
+    }
+}
+
+// shadow rays: visibility of connections, or ghost crossings of edges
+__global__ void __launch_bounds__(kBlock) k_trace_shadow(const __grid_constant__ LaunchArgs A, int it) {
+    __shared__ int s_stack[kStackDepth * kBlock];
+    Ctx c(A, s_stack + threadIdx.x);
+    const WaveBuf &W = A.W;
+    const uint32_t n = min(W.counts[cnt_shadow(it)], W.qa);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t tag = W.a_tag[i];
+        const uint32_t r = tag_root(tag);
+        const int kind = tag_side(tag), step = tag_step(tag);
+        float3 o = f3(W.a_o[i], W.a_o[W.qa + i], W.a_o[2 * W.qa + i]);
+        float3 d = f3(W.a_d[i], W.a_d[W.qa + i], W.a_d[2 * W.qa + i]);
+        const bool ghost = kind >= CK_GHOST_WALK;
+        Hit h;
+        ++c.cnt.rays_shadow;
+        bool hit = scene_trace(c, ghost ? 3 - A.frame : A.frame, o, d, A.S.eps, W.a_tmax[i],
+                               W.a_ex0[i], W.a_ex1[i], true, ghost, h);
+        const uint32_t bit = 1u << step;
+        if (kind == CK_CAMERA && !hit) atomicOr(W.cam_ok + r, bit);
+        else if (kind == CK_NEE && !hit) atomicOr(W.nee_ok + r, bit);
+        else if (kind == CK_GHOST_WALK && hit) atomicOr(W.ghost_w + r, bit);
+        else if (kind == CK_GHOST_NEE && hit) atomicOr(W.ghost_n + r, bit);
+    }
+    if (A.stats) {
+        add_stat(A.stats, ST_RAYS_SHADOW, c.cnt.rays_shadow);
+        add_stat(A.stats, ST_NODES, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS, c.cnt.tris);
+    }
+}
+
+// --- stage B ---------------------------------------------------------------
+
+namespace {
+
+// queue a mapping task for base path (tech, sa, sb) of root r
+__device__ __forceinline__ void dispatch_path(Ctx &c, PathCounts &pc, const Vtx *x, int n,
+                                              uint32_t r, int tech, int sa, int sb) {
+    (void)pc; (void)x; (void)n;
+    const LaunchArgs &A = c.A;
+    uint32_t i = append(A.W.counts + cnt_tasks());
+    if (i < A.W.qt) A.W.tasks[i] = make_int4((int)r, tech, sa, sb);
+}
+
+// the vertices of base path (tech, sa, sb) of root r, read from the slots;
+// returns the vertex count
+__device__ int assemble(const Ctx &c, uint32_t r, int tech, int sa, int sb, Vtx *x) {
+    const WaveBuf &W = c.A.W;
+    const int D = c.A.S.max_depth;
+    x[0] = camera_vertex(c);
+    if (tech == T_1) {                       // (cam, z_t, ..., z_1, x_D, x_L), t = sa
+        const int t = sa;
+        for (int j = 0; j < t; ++j) x[1 + j] = load_vtx(c, W, slot_eye(D, t - j), r);
+        x[t + 1] = load_vtx(c, W, 0, r);
+        x[t + 2] = load_vtx(c, W, 1, r);
+        return t + 3;
+    }
+    if (tech == T_2) {                       // (cam, x_D, y_1, ..., y_s, L_s), s = sb
+        const int s = sb;
+        x[1] = load_vtx(c, W, 0, r);
+        for (int j = 1; j <= s; ++j) x[1 + j] = load_vtx(c, W, slot_light(D, j), r);
+        x[s + 2] = load_vtx(c, W, slot_nee(D, s), r);
+        return s + 3;
+    }
+    if (tech == T_3) {                       // (cam, z_te..z_1, x_D, y_1..y_sl, L_sl)
+        const int te = sa, sl = sb;
+        for (int j = 0; j < te; ++j) x[1 + j] = load_vtx(c, W, slot_eye(D, te - j), r);
+        x[te + 1] = load_vtx(c, W, 0, r);
+        for (int j = 1; j <= sl; ++j) x[te + 1 + j] = load_vtx(c, W, slot_light(D, j), r);
+        x[te + sl + 2] = load_vtx(c, W, slot_nee(D, sl), r);
+        return te + sl + 3;
+    }
+    // path tracing: k = sb vertices (cam, x_1, ..., x_{k-2}, L_{k-2}) or (cam, x_1)
+    const int k = sb;
+    x[1] = load_vtx(c, W, 0, r);
+    if (k == 2) return 2;
+    for (int j = 2; j <= k - 2; ++j) x[j] = load_vtx(c, W, slot_light(D, j - 1), r);
+    x[k - 1] = load_vtx(c, W, slot_nee(D, k - 2), r);
+    return k;
+}
+
+}  // namespace
+
+template <int T>
+__global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs A) {
+    const uint32_t n = A.root_end - A.root_begin;
+    const WaveBuf &W = A.W;
+    Ctx c(A, nullptr);
+    PathCounts pc{0, 0, 0};
+    unsigned int roots = 0;
+    const int D = A.S.max_depth;
+    const int g = A.frame;
+    const bool motion = A.residual && A.E.motion;
+    Vtx ch[kChain], L[kChain], x[kMaxVerts];
+    ChainTables tb;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        ++roots;
+        const uint32_t root = A.root_begin + r;
+        const uint32_t cam = W.cam_ok[r], nee = W.nee_ok[r];
+        if (motion) {
+            // enumerate the non-static base paths into mapping tasks
+            if (T == T_1) {
+                if (!(W.flags[r] & RF_ROOT_OK)) continue;
+                for (int t = 0; t <= W.len_eye[r]; ++t)
+                    if (cam & (1u << t)) dispatch_path(c, pc, x, 0, r, T_1, t, 0);
+            } else if (T == T_2) {
+                if (!(W.flags[r] & RF_ROOT_OK)) continue;
+                for (int s2 = 1; s2 <= W.len_light[r]; ++s2)
+                    if (nee & (1u << s2)) dispatch_path(c, pc, x, 0, r, T_2, 0, s2);
+            } else if (T == T_3) {
+                const int nz = W.len_eye[r], ny = W.len_light[r];
+                for (int te = 1; te <= nz; ++te) {
+                    if (!(cam & (1u << te))) continue;
+                    for (int sl = 1; sl <= ny && te + sl <= D - 2; ++sl)
+                        if (nee & (1u << sl)) dispatch_path(c, pc, x, 0, r, T_3, te, sl);
+                }
+            } else {
+                const int len = W.len_light[r];
+                if (len == 0) continue;
+                const uint32_t gw = W.ghost_w[r], gn = W.ghost_n[r];
+                unsigned dynmask = 0u;
+                for (int j = 1; j <= len; ++j) {
+                    const int prim = W.prim[(size_t)(j == 1 ? 0 : slot_light(D, j - 1)) * W.R + r];
+                    if (prim >= A.S.n_static) dynmask |= 1u << j;
+                }
+                const Vtx x1 = load_vtx(c, W, 0, r);
+                if (!zero3(get_mat(c, g, x1.mat).em) && ((dynmask & 2u) || (gw & 2u)))
+                    dispatch_path(c, pc, x, 0, r, T_7, 0, 2);
+                for (int j = 1; j <= len; ++j) {
+                    if (!(nee & (1u << j))) continue;
+                    const unsigned upto = (2u << j) - 2u;
+                    if ((dynmask & upto) || (gw & upto) || (gn & (1u << j)))
+                        dispatch_path(c, pc, x, 0, r, T_7, 0, j + 2);
+                }
+            }
+            continue;
+        }
+        // no motion (or primal): build the chain, its tables, and evaluate every path
+        int M = 0;
+        unsigned ce = 0u, le = 0u;
+        if (T == T_1) {
+            if (!(W.flags[r] & RF_ROOT_OK)) continue;
+            const int nz = W.len_eye[r];
+            for (int i = 0; i < nz; ++i) {
+                ch[i] = load_vtx(c, W, slot_eye(D, nz - i), r);
+                if (cam & (1u << (nz - i))) ce |= 1u << i;
+            }
+            ch[nz] = load_vtx(c, W, 0, r);
+            if (cam & 1u) ce |= 1u << nz;
+            L[nz] = load_vtx(c, W, 1, r);
+            le = 1u << nz;
+            M = nz + 1;
+        } else if (T == T_2) {
+            if (!(W.flags[r] & RF_ROOT_OK)) continue;
+            const int ny = W.len_light[r];
+            ch[0] = load_vtx(c, W, 0, r);
+            ce = 1u;
+            for (int m = 1; m <= ny; ++m) {
+                ch[m] = load_vtx(c, W, slot_light(D, m), r);
+                if (nee & (1u << m)) {
+                    le |= 1u << m;
+                    L[m] = load_vtx(c, W, slot_nee(D, m), r);
+                }
+            }
+            M = ny + 1;
+        } else if (T == T_3) {
+            const int nz = W.len_eye[r], ny = W.len_light[r];
+            if (nz == 0 || ny == 0) continue;
+            for (int i = 0; i < nz; ++i) {
+                ch[i] = load_vtx(c, W, slot_eye(D, nz - i), r);
+                if (cam & (1u << (nz - i))) ce |= 1u << i;
+            }
+            ch[nz] = load_vtx(c, W, 0, r);
+            for (int m = 1; m <= ny; ++m) {
+                ch[nz + m] = load_vtx(c, W, slot_light(D, m), r);
+                if (nee & (1u << m)) {
+                    le |= 1u << (nz + m);
+                    L[nz + m] = load_vtx(c, W, slot_nee(D, m), r);
+                }
+            }
+            M = nz + ny + 1;
+        } else {
+            const int len = W.len_light[r];
+            if (len == 0) continue;
+            for (int j = 1; j <= len; ++j) {
+                ch[j - 1] = load_vtx(c, W, j == 1 ? 0 : slot_light(D, j - 1), r);
+                if (nee & (1u << j)) {
+                    le |= 1u << (j - 1);
+                    L[j - 1] = load_vtx(c, W, slot_nee(D, j), r);
+                }
+            }
+            ce = 1u;
+            M = len;
+        }
+        build_tables(c, g, 3 - g, A.residual != 0, ch, L, M, ce, le, tb);
+        if (T == T_1) {
+            const int nz = M - 1;
+            for (int t = 0; t <= nz; ++t)
+                if (ce & (1u << (nz - t))) chain_emit(c, pc, tb, nz - t, nz, root, T_1, t, 0);
+        } else if (T == T_2) {
+            for (int s2 = 1; s2 < M; ++s2)
+                if (le & (1u << s2)) chain_emit(c, pc, tb, 0, s2, root, T_2, 0, s2);
+        } else if (T == T_3) {
+            const int nz = W.len_eye[r], ny = W.len_light[r];
+            for (int te = 1; te <= nz; ++te) {
+                if (!(ce & (1u << (nz - te)))) continue;
+                for (int sl = 1; sl <= ny && te + sl <= D - 2; ++sl)
+                    if (le & (1u << (nz + sl)))
+                        chain_emit(c, pc, tb, nz - te, nz + sl, root, T_3, te, sl);
+            }
+        } else {
+            const int tech = A.residual ? T_7 : T_PT;
+            if (!A.residual) {
+                // the camera ray sees an emitter: path (camera, x_1)
+                const float3 em = get_mat(c, g, ch[0].mat).em;
+                if (!zero3(em) && tb.WeG0[0] > 0.f) {
+                    ++pc.paths;
+                    emit(c, root, tech, g, 0, 2, tb.pix[0], em * (tb.WeG0[0] * A.invN / tb.pcam[0]),
+                         -1, f3(0, 0, 0), 0, tb.pcam[0], 0.f, 1.f);
+                }
+            }
+            for (int j = 1; j <= M; ++j) {
+                if (!(le & (1u << (j - 1)))) continue;
+                // without motion a path is static when no vertex lies on the object
+                if (A.residual && !(tb.dyn & ((1u << j) - 1u))) continue;
+                chain_emit(c, pc, tb, 0, j - 1, root, tech, 0, j + 2);
+            }
+        }
+    }
+    if (A.stats) {
+        add_stat(A.stats, ST_ROOTS, roots);
+        add_stat(A.stats, ST_PATHS, pc.paths);
+        add_stat(A.stats, ST_ACCEPTED, pc.accepted);
+        add_stat(A.stats, ST_REJECTED, pc.rejected);
+    }
+}
+
+// --- stage C ---------------------------------------------------------------
+
+__global__ void __launch_bounds__(kBlock) k_map(const __grid_constant__ LaunchArgs A) {
+    __shared__ int s_stack[kStackDepth * kBlock];
+    Ctx c(A, s_stack + threadIdx.x);
+    PathCounts pc{0, 0, 0};
+    const uint32_t n = min(A.W.counts[cnt_tasks()], A.W.qt);
+    Vtx x[kMaxVerts];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 t = A.W.tasks[i];
+        const int k = assemble(c, (uint32_t)t.x, t.y == T_7 ? T_PT : t.y, t.z, t.w, x);
+        evaluate_path(c, pc, A.frame, x, k, A.root_begin + (uint32_t)t.x, t.y, t.z, t.w, true, true);
+    }
+    if (A.stats) {
+        add_stat(A.stats, ST_PATHS, pc.paths);
+        add_stat(A.stats, ST_RAYS_CLOSEST, c.cnt.rays_closest);
+        add_stat(A.stats, ST_RAYS_SHADOW, c.cnt.rays_shadow);
+        add_stat(A.stats, ST_NODES, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS, c.cnt.tris);
+        add_stat(A.stats, ST_ACCEPTED, pc.accepted);
+        add_stat(A.stats, ST_REJECTED, pc.rejected);
+    }
+}
+
+// --- host: one wave --------------------------------------------------------
+
+namespace {
+
+inline int grid_for(uint32_t n, int block, int cap) {
+    uint32_t g = (n + block - 1) / block;
+    return (int)(g < (uint32_t)cap ? (g > 0 ? g : 1) : cap);
+}
+
+template <int T>
+cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
+    const uint32_t n = a.root_end - a.root_begin;
+    const int D = a.S.max_depth;
+    const int gR = grid_for(n, 256, 1 << 20);
+    const int gQ = 152 * 16;                 // persistent-style grids over device-side counts
+    cudaError_t e = cudaMemsetAsync(a.W.counts, 0, sizeof(unsigned int) * kCountSlots, s);
+    if (e != cudaSuccess) return e;
+    k_gen<T><<<gR, 256, 0, s>>>(a);
+    int it0 = 1;
+    if (T == T_1 || T == T_2) {
+        k_trace_shadow<<<gQ, kBlock, 0, s>>>(a, 0);
+        k_start<T><<<gR, 256, 0, s>>>(a);
+        k_trace_shadow<<<gQ, kBlock, 0, s>>>(a, 1);
+        it0 = 1;
+    }
+    // iterations: closest rays pushed at iteration it-1 are traced, extended
+    // into iteration it's rays, and the new shadow rays (slot it+1) traced
+    const int iters = D + 1;
+    for (int it = it0; it <= iters && it + 1 < kMaxIter; ++it) {
+        k_trace_closest<<<gQ, kBlock, 0, s>>>(a, it - 1);
+        k_extend<T><<<gQ, 256, 0, s>>>(a, it);
+        k_trace_shadow<<<gQ, kBlock, 0, s>>>(a, it + 1);
+    }
+    k_eval<T><<<grid_for(n, 128, 1 << 20), 128, 0, s>>>(a);
+    if (a.residual && a.E.motion) k_map<<<gQ, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_wave(int tech, const LaunchArgs &a, cudaStream_t s) {
+    switch (tech) {
+    case 1: return run_wave<T_1>(a, s);
+    case 2: return run_wave<T_2>(a, s);
+    case 3: return run_wave<T_3>(a, s);
+    case 7:
+    case 0: return run_wave<T_PT>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rp

@@ -2,6 +2,7 @@
 // checking and the stream-ordered launches of the path kernels.
 #include "../../include/rp.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -63,10 +64,22 @@ struct rp_scene_s {
     bool stats_on = false;
     double *d_scratch = nullptr;   // FP64 image for the f32 and host entry points
     cudaStream_t last_stream = nullptr;
+    // wavefront buffers (allocated on first use, grown on demand)
+    WaveBuf W{};
+    std::vector<void *> wave_allocs;
+    bool wave_tasks = false;
+    uint32_t wave_cap = 1u << 22;  // roots per wave
+    void free_wave() {
+        for (void *p : wave_allocs) cudaFree(p);
+        wave_allocs.clear();
+        W = WaveBuf{};
+        wave_tasks = false;
+    }
     ~rp_scene_s() {
         for (void *p : allocs) cudaFree(p);
         if (d_stats) cudaFree(d_stats);
         if (d_scratch) cudaFree(d_scratch);
+        free_wave();
     }
 };
 
@@ -152,13 +165,19 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
         return 0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
     };
     // area CDFs: p(x_D) = 1 / A_dyn and p(x_L) = 1 / A_emit
-    std::vector<float> dcdf(nd);
+    // thresholds on the 2^-24 grid of the uniforms: u = k / 2^24 < CDF_i
+    // exactly when k < ceil(CDF_i * 2^24)
+    auto threshold = [](double cdf) -> uint32_t {
+        double t = std::ceil(cdf * 16777216.0);
+        return t >= 16777216.0 ? 16777216u : (uint32_t)t;
+    };
+    std::vector<uint32_t> dcdf(nd);
     double acc = 0.0;
     std::vector<double> dacc(nd);
     for (int i = 0; i < nd; ++i) { acc += area(&dt[3 * (size_t)i]); dacc[i] = acc; }
     const double dyn_area = acc;
-    for (int i = 0; i < nd; ++i) dcdf[i] = (float)(dacc[i] / dyn_area);
-    dcdf[nd - 1] = 1.0f;
+    for (int i = 0; i < nd; ++i) dcdf[i] = threshold(dacc[i] / dyn_area);
+    dcdf[nd - 1] = 16777216u;
     std::vector<int> eids;
     std::vector<double> eacc;
     acc = 0.0;
@@ -173,9 +192,16 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
         delete sc;
         return fail(RP_ERR_INVALID_ARG, "scene needs an emitter and a dynamic object of non-zero area");
     }
-    std::vector<float> ecdf(eids.size());
-    for (size_t i = 0; i < eids.size(); ++i) ecdf[i] = (float)(eacc[i] / acc);
-    ecdf.back() = 1.0f;
+    std::vector<uint32_t> ecdf(eids.size());
+    for (size_t i = 0; i < eids.size(); ++i) ecdf[i] = threshold(eacc[i] / acc);
+    ecdf.back() = 16777216u;
+    // (cos, sin) tables for angles 2 pi k / 2^24 by angle addition
+    std::vector<double2> cs_hi(4096), cs_lo(4096);
+    for (int i = 0; i < 4096; ++i) {
+        const double two_pi = 6.283185307179586476925286766559;
+        cs_hi[i] = make_double2(std::cos(two_pi * i / 4096.0), std::sin(two_pi * i / 4096.0));
+        cs_lo[i] = make_double2(std::cos(two_pi * i / 16777216.0), std::sin(two_pi * i / 16777216.0));
+    }
 
     std::vector<uint32_t> smat(d->static_material, d->static_material + ns);
     std::vector<float> mats(d->materials, d->materials + 12 * (size_t)d->n_materials);
@@ -199,8 +225,11 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
     UP(dt, p4, S.dyn_tri);
     UP(smat, pu, S.stat_mat);
     UP(mats, pf, S.mats);
-    UP(dcdf, pf, S.dyn_cdf);
-    UP(ecdf, pf, S.emit_cdf);
+    UP(dcdf, pu, S.dyn_cdf);
+    UP(ecdf, pu, S.emit_cdf);
+    double2 *pd2;
+    UP(cs_hi, pd2, S.cs_hi);
+    UP(cs_lo, pd2, S.cs_lo);
     UP(eids, pi, S.emit_ids);
 #undef UP
     S.stat.n_nodes = (int)(bs.nodes.size() / 4);
@@ -331,6 +360,7 @@ static LaunchArgs base_args(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64
     a.invN = (float)(1.0 / ((double)spp * sc->S.W * sc->S.H));
     a.tech_mask = (int)mask;
     a.stats = sc->stats_on ? sc->d_stats : nullptr;
+    a.residual = 1;
     return a;
 }
 
@@ -343,8 +373,90 @@ static rp_status check_render(rp_scene *sc, uint32_t spp, uint32_t mask) {
     return RP_OK;
 }
 
+// wavefront buffers for waves of up to R roots; `tasks` adds the mapping
+// task queue needed by edits with motion
+static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
+    const int D = sc->S.max_depth;
+    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return RP_OK;
+    R = std::max(R, sc->W.R);
+    tasks = tasks || sc->wave_tasks;
+    sc->free_wave();
+    WaveBuf &W = sc->W;
+    W.R = R;
+    W.S = slot_count(D);
+    W.qc = 2 * R;
+    W.qa = 3 * R;
+    const int t3 = (D - 3) * (D - 2) / 2;
+    W.qt = tasks ? (uint32_t)std::min<uint64_t>((uint64_t)R * (uint64_t)std::max(D + 1, t3),
+                                                 0xffffffffull)
+                 : 0u;
+    auto alloc = [&](void **p, size_t bytes) -> rp_status {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaErrorMemoryAllocation) return fail(RP_ERR_OOM, "wavefront buffer allocation failed");
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc wavefront");
+        sc->wave_allocs.push_back(*p);
+        return RP_OK;
+    };
+    const size_t SR = (size_t)W.S * R;
+#define A_(ptr, bytes) if (rp_status s_ = alloc((void **)&(ptr), (bytes))) { sc->free_wave(); return s_; }
+    A_(W.px, SR * 4) A_(W.py, SR * 4) A_(W.pz, SR * 4) A_(W.nx, SR * 4) A_(W.ny, SR * 4)
+    A_(W.nz, SR * 4) A_(W.b1, SR * 4) A_(W.b2, SR * 4) A_(W.prim, SR * 4)
+    A_(W.len_eye, R * 4ull) A_(W.len_light, R * 4ull) A_(W.flags, R * 4ull)
+    A_(W.cam_ok, R * 4ull) A_(W.nee_ok, R * 4ull) A_(W.ghost_w, R * 4ull) A_(W.ghost_n, R * 4ull)
+    for (int b = 0; b < 2; ++b) {
+        A_(W.c_o[b], W.qc * 12ull) A_(W.c_d[b], W.qc * 12ull) A_(W.c_ex[b], W.qc * 4ull)
+        A_(W.c_tag[b], W.qc * 4ull)
+    }
+    A_(W.h_prim, W.qc * 4ull) A_(W.h_b1, W.qc * 4ull) A_(W.h_b2, W.qc * 4ull)
+    A_(W.h_p, W.qc * 12ull)
+    A_(W.a_o, W.qa * 12ull) A_(W.a_d, W.qa * 12ull) A_(W.a_tmax, W.qa * 4ull)
+    A_(W.a_ex0, W.qa * 4ull) A_(W.a_ex1, W.qa * 4ull) A_(W.a_tag, W.qa * 4ull)
+    if (tasks) { A_(W.tasks, W.qt * 16ull) }
+    A_(W.counts, kCountSlots * 4ull)
+#undef A_
+    sc->wave_tasks = tasks;
+    return RP_OK;
+}
+
+// run roots [r0, r1) of technique `tech` (0: primal) in frame a.frame as waves
+static rp_status run_waves(rp_scene *sc, LaunchArgs a, int tech, uint32_t r0, uint32_t r1,
+                           cudaStream_t st) {
+    const bool tasks = a.residual && a.E.motion;
+    const uint32_t n = r1 - r0;
+    if (n == 0) return RP_OK;
+    if (rp_status s = ensure_wave(sc, std::min(n, sc->wave_cap), tasks)) return s;
+    a.W = sc->W;
+    for (uint32_t b = r0; b < r1; b += sc->W.R) {
+        a.root_begin = b;
+        a.root_end = std::min(r1, b + sc->W.R);
+        RP_CUDA(launch_wave(tech, a, st), "wavefront launch");
+    }
+    return RP_OK;
+}
+
 static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
                              uint32_t mask, double *d_out, cudaStream_t st) {
+    LaunchArgs a = base_args(sc, E, spp, seed, mask);
+    a.img = d_out;
+    a.residual = 1;
+    const uint32_t N = spp * (uint32_t)(sc->S.W * sc->S.H);
+    if (sc->stats_on)
+        RP_CUDA(cudaMemsetAsync(sc->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, st), "memset");
+    const int techs[4] = {1, 2, 3, 7};
+    for (int g = 1; g <= 2; ++g)
+        for (int t = 0; t < 4; ++t) {
+            if (!(mask & (1u << t))) continue;
+            a.frame = g;
+            if (rp_status s = run_waves(sc, a, techs[t], 0, N, st)) return s;
+        }
+    sc->last_stream = st;
+    return RP_OK;
+}
+
+// the same render with the one-thread-per-root kernels, which need no
+// scratch memory besides the image
+static rp_status render_into_direct(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
+                                    uint32_t mask, double *d_out, cudaStream_t st) {
     LaunchArgs a = base_args(sc, E, spp, seed, mask);
     a.img = d_out;
     a.root_begin = 0;
@@ -422,12 +534,12 @@ extern "C" rp_status rp_render_primal(rp_scene *scene, const rp_edit_handle *edi
     LaunchArgs a = base_args(scene, edit->E, spp, seed, RP_TECH_ALL);
     a.img = d_out;
     a.frame = frame;
-    a.root_begin = 0;
-    a.root_end = spp * (uint32_t)(scene->S.W * scene->S.H);
+    a.residual = 0;
     if (scene->stats_on)
         RP_CUDA(cudaMemsetAsync(scene->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, st),
                 "memset");
-    RP_CUDA(launch_primal(a, st), "primal launch");
+    if (rp_status s = run_waves(scene, a, 0, 0, spp * (uint32_t)(scene->S.W * scene->S.H), st))
+        return s;
     scene->last_stream = st;
     return RP_OK;
 }
@@ -448,13 +560,11 @@ extern "C" rp_status rp_dump_samples(rp_scene *scene, const rp_edit_handle *edit
     RP_CUDA(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st), "memset count");
     LaunchArgs a = base_args(scene, edit->E, spp, seed, tech_mask);
     a.frame = frame;
-    a.root_begin = root_begin;
-    a.root_end = root_end;
+    a.residual = 1;
     a.rec = reinterpret_cast<Record *>(d_records);
     a.rec_cap = capacity;
     a.rec_count = d_count;
-    RP_CUDA(launch_residual(tech, a, st), "dump launch");
-    return RP_OK;
+    return run_waves(scene, a, tech, root_begin, root_end, st);
 }
 
 extern "C" rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edit, int frame,
@@ -522,7 +632,7 @@ rp_status render_residual_into(rp_scene *scene, const rp_edit_handle *edit, uint
                                cudaStream_t stream) {
     if (rp_status s = check_render(scene, spp, tech_mask)) return s;
     if (!edit || !d_img) return fail(RP_ERR_INVALID_ARG, "null edit or image");
-    return render_into(scene, edit->E, spp, seed, tech_mask, d_img, stream);
+    return render_into_direct(scene, edit->E, spp, seed, tech_mask, d_img, stream);
 }
 
 }  // namespace rp

@@ -19,6 +19,10 @@
 
 #include "rp_internal.h"
 
+#ifndef RP_WALK_FP64
+#define RP_WALK_FP64 0
+#endif
+
 namespace rp {
 
 // ---------------------------------------------------------------------------
@@ -58,6 +62,30 @@ static __device__ __forceinline__ float3 linear(const float *M, float3 p) {
 }
 
 constexpr float kPi = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
+
+// double-precision vectors: path vertices and sampled directions are
+// constructed in FP64 and rounded to FP32 once
+static __device__ __forceinline__ double3 d3(double x, double y, double z) { return make_double3(x, y, z); }
+static __device__ __forceinline__ double3 d3(float3 v) { return make_double3(v.x, v.y, v.z); }
+static __device__ __forceinline__ double3 d3(float4 v) { return make_double3(v.x, v.y, v.z); }
+static __device__ __forceinline__ double3 dadd(double3 a, double3 b) { return d3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static __device__ __forceinline__ double3 dsub(double3 a, double3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static __device__ __forceinline__ double3 dscale(double3 a, double s) { return d3(a.x * s, a.y * s, a.z * s); }
+static __device__ __forceinline__ double ddot(double3 a, double3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static __device__ __forceinline__ double3 dcross(double3 a, double3 b) {
+    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static __device__ __forceinline__ double3 dunit(double3 a) { return dscale(a, 1.0 / sqrt(ddot(a, a))); }
+static __device__ __forceinline__ float3 tof(double3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
+static __device__ __forceinline__ double3 daffine(const float *M, double3 p) {
+    return d3(M[0] * p.x + M[1] * p.y + M[2] * p.z + M[3], M[4] * p.x + M[5] * p.y + M[6] * p.z + M[7],
+              M[8] * p.x + M[9] * p.y + M[10] * p.z + M[11]);
+}
+static __device__ __forceinline__ double3 dlinear(const float *M, double3 p) {
+    return d3(M[0] * p.x + M[1] * p.y + M[2] * p.z, M[4] * p.x + M[5] * p.y + M[6] * p.z,
+              M[8] * p.x + M[9] * p.y + M[10] * p.z);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon et al., SC'11)
@@ -193,59 +221,146 @@ static __device__ __forceinline__ float cosine_pdf(float3 n, float3 w) {
     return c > 0.f ? c * (1.0f / kPi) : 0.f;
 }
 
-static __device__ float3 cosine_dir(float3 n, float u1, float u2) {
-    float3 t, b;
-    tangent_frame(n, t, b);
-    float r = sqrtf(u1), ph = 2.0f * kPi * u2;
-    float sp, cp;
-    sincosf(ph, &sp, &cp);
-    float z = sqrtf(fmaxf(0.f, 1.0f - u1));
-    return t * (r * cp) + b * (r * sp) + n * z;
+// tangent frame in double precision (same construction as tangent_frame)
+static __device__ __forceinline__ void tangent_frame_d(double3 n, double3 &t, double3 &b) {
+    const double q00 = 0.727128712871287, q01 = -0.16910891089108918, q02 = 0.6653465346534656;
+    const double q10 = 0.44356435643564374, q11 = 0.85544554455445543, q12 = -0.26732673267326734;
+    const double q20 = -0.52396039603960409, q21 = 0.48950495049504961, q22 = 0.69702970297029698;
+    double3 m = d3(q00 * n.x + q01 * n.y + q02 * n.z, q10 * n.x + q11 * n.y + q12 * n.z,
+                   q20 * n.x + q21 * n.y + q22 * n.z);
+    double sg = m.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + m.z);
+    double c = m.x * m.y * a;
+    double3 tl = d3(1.0 + sg * m.x * m.x * a, sg * c, -sg * m.x);
+    double3 bl = d3(c, sg + m.y * m.y * a, -m.y);
+    t = d3(q00 * tl.x + q10 * tl.y + q20 * tl.z, q01 * tl.x + q11 * tl.y + q21 * tl.z,
+           q02 * tl.x + q12 * tl.y + q22 * tl.z);
+    b = d3(q00 * bl.x + q10 * bl.y + q20 * bl.z, q01 * bl.x + q11 * bl.y + q21 * bl.z,
+           q02 * bl.x + q12 * bl.y + q22 * bl.z);
 }
 
-static __device__ void cosine_inverse(float3 n, float3 w, float &u1, float &u2) {
-    float3 t, b;
-    tangent_frame(n, t, b);
-    float x = dot3(w, t), y = dot3(w, b);
+// cos and sin of 2 pi u in double precision: uniforms on the 2^-24 grid use
+// the angle-addition tables of the scene, other angles sincospi
+static __device__ __forceinline__ void sincos2pi(const DevScene &S, double u, double &s, double &c) {
+    const double k = u * 16777216.0;
+    if (k == floor(k) && k >= 0.0 && k < 16777216.0 && S.cs_hi) {
+        const uint32_t ki = (uint32_t)k;
+        const double2 a = __ldg(&S.cs_hi[ki >> 12]), b = __ldg(&S.cs_lo[ki & 4095u]);
+        c = a.x * b.x - a.y * b.y;
+        s = a.y * b.x + a.x * b.y;
+        return;
+    }
+    sincospi(2.0 * u, &s, &c);
+}
+
+// cosine-distributed direction about n for (u1, u2), in double precision
+static __device__ double3 cosine_dir_d(const DevScene &S, double3 n, double u1, double u2) {
+    double3 t, b;
+    tangent_frame_d(n, t, b);
+    double r = sqrt(u1), sp, cp;
+    sincos2pi(S, u2, sp, cp);
+    double z = sqrt(fmax(0.0, 1.0 - u1));
+    return dadd(dadd(dscale(t, r * cp), dscale(b, r * sp)), dscale(n, z));
+}
+
+static __device__ float3 cosine_dir(const DevScene &S, float3 n, double u1, double u2) {
+    return tof(cosine_dir_d(S, d3(n), u1, u2));
+}
+
+static __device__ void cosine_inverse(float3 n, float3 w, double &u1, double &u2) {
+    double3 t, b;
+    tangent_frame_d(d3(n), t, b);
+    double3 wd = d3(w);
+    double x = ddot(wd, t), y = ddot(wd, b);
     u1 = x * x + y * y;
-    float a = atan2f(y, x) * (0.5f / kPi);
-    u2 = a < 0.f ? a + 1.0f : a;
+    double a = atan2(y, x) / (2.0 * kPiD);
+    u2 = a < 0.0 ? a + 1.0 : a;
 }
 
-static __device__ bool bsdf_sample(const Mat &m, float3 n, float3 wc, float u1, float u2, float3 &wo) {
-    if (dot3(n, wc) <= 0.f) return false;
+// sample wo at a surface with conditioning direction wc; false on failure
+static __device__ bool bsdf_sample(const DevScene &S, const Mat &m, float3 n, float3 wc, double u1,
+                                   double u2, float3 &wo) {
+    const double3 nd = d3(n), wcd = d3(wc);
+    if (ddot(nd, wcd) <= 0.0) return false;
     if (m.type == 0) {
-        wo = cosine_dir(n, u1, u2);
+        double3 w = cosine_dir_d(S, nd, u1, u2);
+        if (ddot(nd, w) <= 0.0) return false;
+        wo = tof(w);
+        return true;
+    }
+    double a2 = (double)m.alpha * (double)m.alpha;
+    double c2 = (1.0 - u1) / (1.0 + (a2 - 1.0) * u1);
+    double ct = sqrt(c2), st = sqrt(fmax(0.0, 1.0 - c2)), sp, cp;
+    sincos2pi(S, u2, sp, cp);
+    double3 t, b;
+    tangent_frame_d(nd, t, b);
+    double3 h = dadd(dadd(dscale(t, st * cp), dscale(b, st * sp)), dscale(nd, ct));
+    double d = ddot(wcd, h);
+    if (d <= 0.0) return false;
+    double3 w = dsub(dscale(h, 2.0 * d), wcd);
+    if (ddot(nd, w) <= 0.0) return false;
+    wo = tof(w);
+    return true;
+}
+
+// the same sampler in single precision, for the random walks (uniforms on
+// the 2^-24 grid, trigonometry by sincospif)
+static __device__ bool bsdf_sample_walk(const DevScene &S, const Mat &m, float3 n, float3 wc, float u1,
+                                        float u2, float3 &wo) {
+#if RP_WALK_FP64
+    return bsdf_sample(S, m, n, wc, u1, u2, wo);
+#else
+    (void)S;
+    if (dot3(n, wc) <= 0.f) return false;
+    float3 t, b;
+    tangent_frame(n, t, b);
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    if (m.type == 0) {
+        float r = sqrtf(u1), z = sqrtf(fmaxf(0.f, 1.0f - u1));
+        wo = t * (r * cp) + b * (r * sp) + n * z;
         return dot3(n, wo) > 0.f;
     }
     float a2 = m.alpha * m.alpha;
     float c2 = (1.0f - u1) / (1.0f + (a2 - 1.0f) * u1);
-    float ct = sqrtf(c2), st = sqrtf(fmaxf(0.f, 1.0f - c2)), ph = 2.0f * kPi * u2;
-    float sp, cp;
-    sincosf(ph, &sp, &cp);
-    float3 t, b;
-    tangent_frame(n, t, b);
+    float ct = sqrtf(c2), st = sqrtf(fmaxf(0.f, 1.0f - c2));
     float3 h = t * (st * cp) + b * (st * sp) + n * ct;
     float d = dot3(wc, h);
     if (d <= 0.f) return false;
     wo = h * (2.0f * d) - wc;
     return dot3(n, wo) > 0.f;
+#endif
 }
 
-static __device__ void bsdf_inverse(const Mat &m, float3 n, float3 wc, float3 wo, float &u1, float &u2) {
+static __device__ float3 cosine_dir_walk(const DevScene &S, float3 n, float u1, float u2) {
+#if RP_WALK_FP64
+    return cosine_dir(S, n, u1, u2);
+#else
+    (void)S;
+    float3 t, b;
+    tangent_frame(n, t, b);
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    float r = sqrtf(u1), z = sqrtf(fmaxf(0.f, 1.0f - u1));
+    return t * (r * cp) + b * (r * sp) + n * z;
+#endif
+}
+
+// the numbers (u1, u2) for which bsdf_sample produces wo
+static __device__ void bsdf_inverse(const Mat &m, float3 n, float3 wc, float3 wo, double &u1, double &u2) {
     if (m.type == 0) {
         cosine_inverse(n, wo, u1, u2);
         return;
     }
-    float a2 = m.alpha * m.alpha;
-    float3 h = unit3(wc + wo);
-    float3 t, b;
-    tangent_frame(n, t, b);
-    float hx = dot3(h, t), hy = dot3(h, b), hz = dot3(h, n);
-    float c2 = hz * hz;
-    u1 = (1.0f - c2) / (1.0f + c2 * (a2 - 1.0f));
-    float a = atan2f(hy, hx) * (0.5f / kPi);
-    u2 = a < 0.f ? a + 1.0f : a;
+    double a2 = (double)m.alpha * (double)m.alpha;
+    double3 h = dunit(dadd(d3(wc), d3(wo)));
+    double3 t, b;
+    tangent_frame_d(d3(n), t, b);
+    double hx = ddot(h, t), hy = ddot(h, b), hz = ddot(h, d3(n));
+    double c2 = hz * hz;
+    u1 = (1.0 - c2) / (1.0 + c2 * (a2 - 1.0));
+    double a = atan2(hy, hx) / (2.0 * kPiD);
+    u2 = a < 0.0 ? a + 1.0 : a;
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +370,7 @@ static __device__ void bsdf_inverse(const Mat &m, float3 n, float3 wc, float3 wo
 struct Hit {
     float t, b1, b2;
     int prim;
+    float3 p;      // closest hits: the intersection point recomputed in double
 };
 
 struct Counters {
@@ -420,6 +536,36 @@ static __device__ __forceinline__ Mat get_mat(const Ctx &c, int frame, int mat) 
     return load_mat(c.A.S.mats + 12 * mat);
 }
 
+// the closest hit recomputed in double: Moller-Trumbore on the hit triangle
+// (in object space for the dynamic object), position rounded once
+static __device__ void refine_hit(const Ctx &c, int g, float3 o, float3 d, Hit &h) {
+    const DevScene &S = c.A.S;
+    const bool dyn = h.prim >= S.n_static;
+    const float4 *tri = dyn ? S.dyn_tri + 3 * (h.prim - S.n_static) : S.stat_tri + 3 * h.prim;
+    double3 od = d3(o), dd = d3(d);
+    if (dyn) {
+        od = daffine(c.A.E.Minv[g], od);
+        dd = dlinear(c.A.E.Minv[g], dd);
+    }
+    const double3 v0 = d3(tri[0]), e1 = dsub(d3(tri[1]), v0), e2 = dsub(d3(tri[2]), v0);
+    const double3 pv = dcross(dd, e2);
+    const double det = ddot(e1, pv);
+    if (det == 0.0) {
+        h.p = o + d * h.t;
+        return;
+    }
+    const double inv = 1.0 / det;
+    const double3 sv = dsub(od, v0);
+    const double u = ddot(sv, pv) * inv;
+    const double3 qv = dcross(sv, e1);
+    const double v = ddot(dd, qv) * inv;
+    double3 p = dadd(dadd(v0, dscale(e1, u)), dscale(e2, v));
+    if (dyn) p = daffine(c.A.E.M[g], p);
+    h.p = tof(p);
+    h.b1 = (float)u;
+    h.b2 = (float)v;
+}
+
 // query of the scene in frame g: static BVH and the dynamic BVH under M_g
 static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin, float tmax, int ex0,
                             int ex1, bool any, bool dyn_only, Hit &h) {
@@ -435,6 +581,7 @@ static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin
         if (traverse(S.dyn, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow))
             found = true;
     }
+    if (found && !any) refine_hit(c, g, o, d, h);
     return found;
 }
 
@@ -454,28 +601,52 @@ static __device__ __forceinline__ bool is_dyn(const Ctx &c, const Vtx &v) {
 }
 
 // the surface point with barycentrics (b1, b2) on triangle `prim` in frame
-// g; unit normals come from the scene tables (computed in double on the host,
-// stored in the .w slots of the three vertex records)
-static __device__ Vtx make_vertex(const Ctx &c, int g, int prim, float b1, float b2) {
+// g, combined in double and rounded once; unit normals come from the scene
+// tables (computed in double on the host, stored in the .w slots)
+static __device__ Vtx make_vertex_d(const Ctx &c, int g, int prim, double b1, double b2) {
     const DevScene &S = c.A.S;
     Vtx v;
     if (prim < S.n_static) {
         const float4 a = S.stat_tri[3 * prim], b = S.stat_tri[3 * prim + 1],
                      d = S.stat_tri[3 * prim + 2];
-        float3 v0 = xyz(a);
-        v.p = v0 + (xyz(b) - v0) * b1 + (xyz(d) - v0) * b2;
+        double3 v0 = d3(a);
+        v.p = tof(dadd(dadd(v0, dscale(dsub(d3(b), v0), b1)), dscale(dsub(d3(d), v0), b2)));
         v.n = f3(a.w, b.w, d.w);
         v.mat = (int)S.stat_mat[prim];
     } else {
         const int q = prim - S.n_static;
         const float4 a = S.dyn_tri[3 * q], b = S.dyn_tri[3 * q + 1], d = S.dyn_tri[3 * q + 2];
-        float3 v0 = xyz(a);
-        float3 po = v0 + (xyz(b) - v0) * b1 + (xyz(d) - v0) * b2;
+        double3 v0 = d3(a);
+        double3 po = dadd(dadd(v0, dscale(dsub(d3(b), v0), b1)), dscale(dsub(d3(d), v0), b2));
         const float *M = c.A.E.M[g];
-        v.p = affine(M, po);
-        v.n = linear(M, f3(a.w, b.w, d.w));
+        v.p = tof(daffine(M, po));
+        v.n = tof(dlinear(M, d3(a.w, b.w, d.w)));
         v.mat = kMatDynamic;
     }
+    v.prim = prim;
+    v.b1 = (float)b1;
+    v.b2 = (float)b2;
+    return v;
+}
+
+static __device__ __forceinline__ Vtx make_vertex(const Ctx &c, int g, int prim, float b1, float b2) {
+    return make_vertex_d(c, g, prim, (double)b1, (double)b2);
+}
+
+// a vertex at a known (refined) position p on triangle `prim`
+static __device__ Vtx make_vertex_at(const Ctx &c, int g, int prim, float b1, float b2, float3 p) {
+    const DevScene &S = c.A.S;
+    Vtx v;
+    if (prim < S.n_static) {
+        v.n = f3(S.stat_tri[3 * prim].w, S.stat_tri[3 * prim + 1].w, S.stat_tri[3 * prim + 2].w);
+        v.mat = (int)S.stat_mat[prim];
+    } else {
+        const int q = prim - S.n_static;
+        v.n = tof(dlinear(c.A.E.M[g], d3(S.dyn_tri[3 * q].w, S.dyn_tri[3 * q + 1].w,
+                                          S.dyn_tri[3 * q + 2].w)));
+        v.mat = kMatDynamic;
+    }
+    v.p = p;
     v.prim = prim;
     v.b1 = b1;
     v.b2 = b2;
@@ -497,9 +668,9 @@ static __device__ __forceinline__ Vtx camera_vertex(const Ctx &c) {
 // ---------------------------------------------------------------------------
 
 static __device__ __forceinline__ float3 camera_dir(const DevScene &S, int px, int py, float jx, float jy) {
-    float sx = (2.0f * ((float)px + jx) / (float)S.W - 1.0f) * S.hw;
-    float sy = (1.0f - 2.0f * ((float)py + jy) / (float)S.H) * S.hh;
-    return unit3(S.cam_fwd + S.cam_right * sx + S.cam_up * sy);
+    double sx = (2.0 * ((double)px + jx) / (double)S.W - 1.0) * (double)S.hw;
+    double sy = (1.0 - 2.0 * ((double)py + jy) / (double)S.H) * (double)S.hh;
+    return tof(dunit(dadd(dadd(d3(S.cam_fwd), dscale(d3(S.cam_right), sx)), dscale(d3(S.cam_up), sy))));
 }
 
 static __device__ __forceinline__ int camera_project(const DevScene &S, float3 p, float &cosc) {
@@ -637,7 +808,7 @@ static __device__ bool trace_next(Ctx &c, int g, const Vtx &a, float3 d, Vtx &ou
     if (!scene_trace(c, g, a.p, d, c.A.S.eps, __int_as_float(0x7f800000), a.prim, -1, false, false,
                      h))
         return false;
-    out = make_vertex(c, g, h.prim, h.b1, h.b2);
+    out = make_vertex_at(c, g, h.prim, h.b1, h.b2, h.p);
     return true;
 }
 
@@ -694,18 +865,18 @@ static __device__ int map_step(Ctx &c, int g, int g2, const Vtx *x, Vtx *y, int 
     }
     // random-seed replay through the inverse of the step's sampling routine
     float3 wo = unit3(x[b].p - x[a].p);
-    float u1, u2;
+    double u1, u2;
     float3 w2;
     Mat ma = get_mat(c, g, x[a].mat), mya = get_mat(c, g2, y[a].mat);
     if (cc < 0) {
         cosine_inverse(x[a].n, wo, u1, u2);
-        w2 = cosine_dir(y[a].n, u1, u2);
+        w2 = cosine_dir(c.A.S, y[a].n, u1, u2);
         if (dot3(y[a].n, w2) <= 0.f) return MAP_INVALID;
     } else {
         float3 wc = unit3(x[cc].p - x[a].p);
         bsdf_inverse(ma, x[a].n, wc, wo, u1, u2);
         float3 wc2 = unit3(y[cc].p - y[a].p);
-        if (!bsdf_sample(mya, y[a].n, wc2, u1, u2, w2)) return MAP_INVALID;
+        if (!bsdf_sample(c.A.S, mya, y[a].n, wc2, u1, u2, w2)) return MAP_INVALID;
     }
     Vtx nb;
     if (!trace_next(c, g2, y[a], w2, nb)) return MAP_INVALID;
@@ -827,8 +998,9 @@ struct PathCounts {
     unsigned int paths, accepted, rejected;
 };
 
+// static_known: the caller already rejected static paths of technique (7)
 static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x, int n, uint32_t root,
-                              int tech, int sa, int sb, bool residual) {
+                              int tech, int sa, int sb, bool residual, bool static_known = false) {
     int pa;
     float3 fx = path_throughput(c, g, x, n, pa);
     if (zero3(fx)) return;
@@ -849,7 +1021,7 @@ static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x
         emit(c, root, tech, g, sa, sb, pa, fx * (invN / p), -1, f3(0, 0, 0), 0, p, 0.f, 1.f);
         return;
     }
-    if (tech == T_7 && path_is_static(c, g, x, n)) return;
+    if (tech == T_7 && !static_known && path_is_static(c, g, x, n)) return;
     ++pc.paths;
     const float Pg = mis_denominator(c, g, x, n);
     const float sign = (g == 2) ? 1.0f : -1.0f;
@@ -896,36 +1068,38 @@ static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x
 // root sampling and walks
 // ---------------------------------------------------------------------------
 
-static __device__ __forceinline__ int cdf_pick(const float *cdf, int n, float u) {
+// the triangle of uniform u = k / 2^24: smallest i with k < cdf[i]
+static __device__ __forceinline__ int cdf_pick(const uint32_t *cdf, int n, float u) {
+    const uint32_t k = (uint32_t)(u * 16777216.0f);
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (u < __ldg(&cdf[mid])) hi = mid;
+        if (k < __ldg(&cdf[mid])) hi = mid;
         else lo = mid + 1;
     }
     return lo;
 }
 
-static __device__ __forceinline__ void tri_sample(float u1, float u2, float &b1, float &b2) {
-    float s = sqrtf(u1);
-    b1 = s * (1.0f - u2);
-    b2 = s * u2;
+static __device__ __forceinline__ void tri_sample(float u1, float u2, double &b1, double &b2) {
+    double s = sqrt((double)u1);
+    b1 = s * (1.0 - (double)u2);
+    b2 = s * (double)u2;
 }
 
 static __device__ Vtx sample_dynamic(const Ctx &c, int g, float4 r) {
     const DevScene &S = c.A.S;
     int t = cdf_pick(S.dyn_cdf, S.n_dyn, r.x);
-    float b1, b2;
+    double b1, b2;
     tri_sample(r.y, r.z, b1, b2);
-    return make_vertex(c, g, S.n_static + t, b1, b2);
+    return make_vertex_d(c, g, S.n_static + t, b1, b2);
 }
 
 static __device__ Vtx sample_emitter(const Ctx &c, int g, float4 r) {
     const DevScene &S = c.A.S;
     int t = cdf_pick(S.emit_cdf, S.n_emit, r.x);
-    float b1, b2;
+    double b1, b2;
     tri_sample(r.y, r.z, b1, b2);
-    return make_vertex(c, g, S.emit_ids[t], b1, b2);
+    return make_vertex_d(c, g, S.emit_ids[t], b1, b2);
 }
 
 static __device__ __forceinline__ bool faces(const Vtx &v, float3 towards) {
@@ -950,7 +1124,7 @@ static __device__ bool walk_step(Ctx &c, int g, const Vtx &prev, const Vtx &at, 
     float3 wc = unit3(prev.p - at.p);
     float3 wo;
     Mat m = get_mat(c, g, at.mat);
-    if (!bsdf_sample(m, at.n, wc, r.x, r.y, wo)) return false;
+    if (!bsdf_sample_walk(c.A.S, m, at.n, wc, r.x, r.y, wo)) return false;
     if (!trace_next(c, g, at, wo, out)) return false;
     if (dot3(out.n, wo) >= 0.f) return false;
     return true;
@@ -1024,7 +1198,7 @@ static __device__ void root_T3(Ctx &c, PathCounts &pc, int g, uint32_t root) {
     zv[0] = yv[0];
     {
         float4 r = draw(seed, root, T_3, g, SD_LIGHT, 1);
-        float3 w = cosine_dir(yv[0].n, r.x, r.y);
+        float3 w = cosine_dir_walk(c.A.S, yv[0].n, r.x, r.y);
         if (dot3(yv[0].n, w) > 0.f && trace_next(c, g, yv[0], w, yv[1]) &&
             dot3(yv[1].n, w) < 0.f && !vtx_black(c, g, yv[1])) {
             ny = 1;

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "rp_wave.h"
+
 namespace rp {
 
 constexpr int kMaxDepth = 10;          // maximum path edges accepted by the API
@@ -33,8 +35,11 @@ struct DevScene {
     const float4 *dyn_tri;      // [n_dyn][3] object-space vertices by triangle id; .w = unit normal
     const uint32_t *stat_mat;   // [n_static] material index
     const float *mats;          // [n_mats][12]
-    const float *dyn_cdf;       // [n_dyn] area CDF of the dynamic object
-    const float *emit_cdf;      // [n_emit] area CDF of the emitters
+    const uint32_t *dyn_cdf;    // [n_dyn] area CDF thresholds of the dynamic object, see below
+    const uint32_t *emit_cdf;   // [n_emit] area CDF thresholds of the emitters
+    // uniforms are k / 2^24; triangle i is picked for the smallest i with
+    // k < cdf[i], where cdf[i] = ceil(CDF_i * 2^24) in double precision
+    const double2 *cs_hi, *cs_lo;   // (cos, sin) of 2 pi h / 2^12 and 2 pi l / 2^24, h, l < 4096
     const int *emit_ids;        // [n_emit] static triangle ids
     int n_static, n_dyn, n_emit, n_mats;
     float dyn_area, emit_area;
@@ -81,6 +86,8 @@ struct LaunchArgs {
     unsigned long long rec_cap;
     unsigned long long *rec_count;
     unsigned long long *stats;  // ST_COUNT counters or null
+    WaveBuf W;                  // wavefront buffers (wavefront mode)
+    int residual;               // 1: residual techniques, 0: primal path tracing
 };
 
 // launchers implemented in the .cu files
@@ -92,5 +99,8 @@ cudaError_t launch_trace(const DevScene &S, const DevEdit &E, int frame, uint32_
 cudaError_t launch_philox(uint32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                           cudaStream_t s);
 cudaError_t launch_add_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t s);
+// one wave [root_begin, root_end) of one technique (0 = primal path tracing)
+// in frame a.frame through the wavefront kernels
+cudaError_t launch_wave(int tech, const LaunchArgs &a, cudaStream_t s);
 
 }  // namespace rp

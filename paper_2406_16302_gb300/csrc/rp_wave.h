@@ -1,0 +1,73 @@
+// Wavefront buffers: per-root vertex slots and flags, SoA ray queues and the
+// mapping task queue.  Owned by a scene, reused across renders.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rp {
+
+// Vertex slots of one root (D = max depth):
+//   0            root vertex: x_D (techniques 1-3) or x_1 (path tracing)
+//   1            x_L of technique (1)
+//   2 + m - 1    eye-side walk vertex z_m,   m = 1 .. D-2
+//   D + m - 1    light-side walk vertex y_m, m = 1 .. D-2 (path tracing: x_{m+1})
+//   2D-2 + m-1   next-event vertex L_m,      m = 1 .. D-1
+__host__ __device__ __forceinline__ int slot_count(int D) { return 3 * D - 3; }
+__host__ __device__ __forceinline__ int slot_eye(int D, int m) { (void)D; return 2 + m - 1; }
+__host__ __device__ __forceinline__ int slot_light(int D, int m) { return D + m - 1; }
+__host__ __device__ __forceinline__ int slot_nee(int D, int m) { return 2 * D - 2 + m - 1; }
+
+// ray tags: wave-local root (24 bits) | side or connection kind (2 bits) |
+// step (4 bits)
+__host__ __device__ __forceinline__ uint32_t make_tag(uint32_t r, int side, int step) {
+    return r | ((uint32_t)side << 24) | ((uint32_t)step << 26);
+}
+__host__ __device__ __forceinline__ uint32_t tag_root(uint32_t t) { return t & 0xffffffu; }
+__host__ __device__ __forceinline__ int tag_side(uint32_t t) { return (int)((t >> 24) & 3u); }
+__host__ __device__ __forceinline__ int tag_step(uint32_t t) { return (int)((t >> 26) & 15u); }
+
+// connection kinds of shadow rays
+enum { CK_CAMERA = 0, CK_NEE = 1, CK_GHOST_WALK = 2, CK_GHOST_NEE = 3 };
+
+// per-root flag bits
+enum { RF_ROOT_OK = 1 };
+
+constexpr int kMaxIter = 16;      // counter slots per queue
+
+struct WaveBuf {
+    uint32_t R;                    // root capacity of a wave
+    int S;                         // vertex slots per root
+    // vertex slots, [S][R]
+    float *px, *py, *pz, *nx, *ny, *nz, *b1, *b2;
+    int *prim;
+    // per-root state, [R]
+    int *len_eye, *len_light, *flags;
+    uint32_t *cam_ok, *nee_ok, *ghost_w, *ghost_n;
+    // closest-hit ray queues (double-buffered) and their hits, capacity qc
+    uint32_t qc;
+    float *c_o[2], *c_d[2];        // [3][qc] each (x plane, then y, then z)
+    int *c_ex[2];
+    uint32_t *c_tag[2];
+    int *h_prim;
+    float *h_b1, *h_b2;
+    float *h_p;                    // [3][qc] refined hit positions
+    // shadow-ray queue, capacity qa
+    uint32_t qa;
+    float *a_o, *a_d, *a_tmax;     // a_o, a_d: [3][qa]
+    int *a_ex0, *a_ex1;
+    uint32_t *a_tag;
+    int a_dyn_frame;               // unused placeholder for alignment
+    // mapping tasks: (root, technique, sa, sb)
+    uint32_t qt;
+    int4 *tasks;
+    // counters: closest [kMaxIter], shadow [kMaxIter], tasks [1]
+    unsigned int *counts;
+};
+
+__host__ __device__ __forceinline__ int cnt_closest(int it) { return it; }
+__host__ __device__ __forceinline__ int cnt_shadow(int it) { return kMaxIter + it; }
+__host__ __device__ __forceinline__ int cnt_tasks() { return 2 * kMaxIter; }
+constexpr int kCountSlots = 2 * kMaxIter + 1;
+
+}  // namespace rp

@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "librp.so")
+LIB_PATH = os.environ.get("RP_LIBRARY") or os.path.join(HERE, "_build", "librp.so")
 
 RP_OK = 0
 RP_TECH_ALL = 15
