@@ -6,7 +6,7 @@ blob that changes from Lambert (albedo 0.8) to GGX (alpha 0.3, F0 0.04);
 techniques (1), (2), (3) and path tracing with rejection, both frames.
 
 One step = one residual render of the whole image (every root of every
-technique in both frames: 8 kernel launches).  A residual sample = one root
+technique in both frames), i.e. one rp_render_residual call.  A residual sample = one root
 of one technique in one frame, with every base path it generates, their
 mapped paths, MIS denominators and splats; a step processes
 spp * W * H * 4 * 2 of them.
@@ -39,8 +39,13 @@ FLOP_PER_NODE = 2 * (6 * 2 + 12 + 2)
 FLOP_PER_TRI = 9 + 6 * 2 + 9 + 2 + 6 + 2 * 2 + 1 + 3
 # GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA per clock
 SMS, FP32_LANES = 152, 128
+# algorithmic bytes of the traversal kernels, no cache credit: a node visit
+# reads one 64-byte two-child node, a triangle test one 48-byte triangle; a
+# closest-hit ray reads its 32-byte queue entry and writes a 28-byte hit, a
+# shadow ray reads a 40-byte entry
+BYTES_PER_NODE, BYTES_PER_TRI = 64, 48
+BYTES_PER_RAY = {"k_trace_closest": 32 + 28, "k_trace_shadow": 40}
 
-TECHS = [(1, 1), (2, 2), (3, 4), (7, 8)]   # (technique, mask bit)
 
 
 def workload(name):
@@ -229,44 +234,43 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2
     seed0 = 1000 * (rank + 1)
 
-    # algorithmic work per technique launch pair (untimed counting pass)
+    # algorithmic work of one step (untimed counting pass)
     rp.rp_enable_stats(sc, True)
-    work = {}
-    for tech, mask in TECHS:
-        rp.rp_render_residual(sc, ed, spp, seed0, out, tech_mask=mask)
-        work[tech] = rp.rp_get_stats(sc)
+    rp.rp_render_residual(sc, ed, spp, seed0, out, stream=stream)
+    work = rp.rp_get_stats(sc)
     rp.rp_enable_stats(sc, False)
 
-    def step(seed, events=None):
-        for tech, mask in TECHS:
-            if events is not None:
-                events[tech][0].record(stream)
-            rp.rp_render_residual(sc, ed, spp, seed, out, tech_mask=mask, stream=stream)
-            if events is not None:
-                events[tech][1].record(stream)
+    def step(seed):
+        rp.rp_render_residual(sc, ed, spp, seed, out, stream=stream)
 
     for w in range(args.warmup):
         step(seed0 + 1 + w)
     torch.cuda.synchronize()
-    per_tech = {t: 0.0 for t, _ in TECHS}
+    rp.rp_get_kernel_times(sc)                     # discard
+    rp.rp_enable_timing(sc, True)
     step_ms = []
+    kern = {}
     with ClockSampler(local) as clk:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.zero_()                       # evict L2 between timed steps
-            ev = {t: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for t, _ in TECHS}
-            step(seed0 + 100 + k, ev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(seed0 + 100 + k)
+            e1.record(stream)
             torch.cuda.synchronize()
-            ms = {t: ev[t][0].elapsed_time(ev[t][1]) for t, _ in TECHS}
-            for t in ms:
-                per_tech[t] += ms[t]
-            step_ms.append(sum(ms.values()))
+            step_ms.append(e0.elapsed_time(e1))
+            for name, (n, ms) in rp.rp_get_kernel_times(sc).items():
+                a_ = kern.setdefault(name, [0, 0.0])
+                a_[0] += n
+                a_[1] += ms
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+    rp.rp_enable_timing(sc, False)
     my_ms = float(np.mean(step_ms))
     worst_ms = my_ms
     if dist:
@@ -274,6 +278,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         worst_ms = float(t.item())
     value = samples_per_step * ws / (worst_ms / 1e3)
+    launches_per_step = sum(n for n, _ in kern.values()) / args.steps
 
     # end to end through the host-buffer entry point: edit upload, render,
     # image copy back, every step
@@ -296,26 +301,44 @@ def main():
                "h2d_bytes_per_step": 4 * 48, "d2h_bytes_per_step": int(host.nbytes),
                "ms_per_step": e_ms}
 
-    # roofline of the dominant kernel (the technique with the largest time)
-    dom = max(per_tech, key=per_tech.get)
-    dom_ms = per_tech[dom] / args.steps / 2          # one launch per frame
-    w = work[dom]
-    flops_launch = (w["nodes_visited"] * FLOP_PER_NODE + w["tris_tested"] * FLOP_PER_TRI) / 2
+    # roofline of the dominant traversal kernel (node box tests and triangle
+    # tests at the FP32 peak); every kernel's share is reported beside it
+    per_kernel = {k: {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
+                      "share": ms / max(sum(v[1] for v in kern.values()), 1e-9)}
+                  for k, (n, ms) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    trav = {"k_trace_closest": (work["nodes_closest"], work["tris_closest"], work["rays_closest"]),
+            "k_trace_shadow": (work["nodes_shadow"], work["tris_shadow"], work["rays_shadow"])}
+    dom = max(trav, key=lambda k: kern.get(k, (0, 0.0))[1])
+    n_launch, ms_tot = kern[dom]
+    launch_ms = ms_tot / n_launch
+    nodes, tris, rays = trav[dom]
+    launches_one_step = n_launch / args.steps
+    bytes_launch = (nodes * BYTES_PER_NODE + tris * BYTES_PER_TRI
+                    + rays * BYTES_PER_RAY[dom]) / launches_one_step
+    flops_launch = (nodes * FLOP_PER_NODE + tris * FLOP_PER_TRI) / launches_one_step
     peaks = measured_peaks()
     clock = clk.summary()
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = SMS * FP32_LANES * 2 * peak_mhz * 1e6 / 1e12
-    achieved = flops_launch / (dom_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": f"k_roots_{dom}", "launch_ms": dom_ms,
-                "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {peak_mhz:.0f} MHz "
-                              "(sm_max_mhz of MEASURED_PEAKS.json)",
-                "work_per_launch": {"node_visits": w["nodes_visited"] // 2,
-                                    "triangle_tests": w["tris_tested"] // 2,
-                                    "rays": (w["rays_closest"] + w["rays_shadow"]) // 2,
-                                    "flop_per_node": FLOP_PER_NODE, "flop_per_tri": FLOP_PER_TRI},
-                "share_of_step": per_tech[dom] / sum(per_tech.values())}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_launch / (launch_ms / 1e3) / 1e9
+    achieved_tf = flops_launch / (launch_ms / 1e3) / 1e12
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": dom, "launch_ms": launch_ms,
+                "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (measured copy bandwidth)"
+                              if "hbm_gbs" in peaks else "fallback 6800 GB/s",
+                "bytes_per_launch": bytes_launch,
+                "work_per_launch": {"node_visits": nodes / launches_one_step,
+                                    "triangle_tests": tris / launches_one_step,
+                                    "rays": rays / launches_one_step,
+                                    "bytes_per_node": BYTES_PER_NODE, "bytes_per_tri": BYTES_PER_TRI,
+                                    "bytes_per_ray": BYTES_PER_RAY[dom]},
+                "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": peak_tflops,
+                         "frac": achieved_tf / peak_tflops,
+                         "basis": f"152 SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz; "
+                                  f"{FLOP_PER_NODE} flop per node, {FLOP_PER_TRI} per triangle"},
+                "share_of_step": ms_tot / max(sum(v[1] for v in kern.values()), 1e-9)}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -334,9 +357,11 @@ def main():
                    "techniques": "1,2,3,7", "roots_per_technique_frame": N,
                    "samples_per_step": samples_per_step, "accumulation": "fp64 atomics",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "per_technique_ms": {str(t): per_tech[t] / args.steps for t in per_tech}},
+                   "per_kernel": per_kernel,
+                   "rays_per_step": work["rays_closest"] + work["rays_shadow"],
+                   "paths_per_step": work["paths"]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 8 * args.steps, "clocks": clock,
+        "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clock,
     }
     print(json.dumps(line), flush=True)
     if dist:

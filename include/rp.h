@@ -206,12 +206,29 @@ typedef struct {
     unsigned long long roots;
     unsigned long long paths;
     unsigned long long rays_closest, rays_shadow;
-    unsigned long long nodes_visited, tris_tested;
+    unsigned long long nodes_visited, tris_tested;      /* all traversals */
     unsigned long long accepted, rejected;
+    unsigned long long nodes_closest, tris_closest;     /* closest-hit trace kernel */
+    unsigned long long nodes_shadow, tris_shadow;       /* shadow-ray trace kernel */
 } rp_stats;
 
 rp_status rp_enable_stats(rp_scene *scene, int on);
 rp_status rp_get_stats(rp_scene *scene, rp_stats *out);
+
+/* Per-kernel device times of the wavefront kernels: when enabled, every
+ * launch on a scene is bracketed by CUDA events recorded on its stream.
+ * rp_get_kernel_times synchronises the scene's last stream, writes up to
+ * `capacity` entries (kernel name, launches, milliseconds summed over the
+ * launches since the previous call) and resets the sums; *count receives the
+ * number of kernels. */
+typedef struct {
+    char name[32];
+    unsigned long long launches;
+    double ms;
+} rp_kernel_time;
+
+rp_status rp_enable_timing(rp_scene *scene, int on);
+rp_status rp_get_kernel_times(rp_scene *scene, rp_kernel_time *out, int capacity, int *count);
 
 /* Thread-local message describing the last error (empty string if none). */
 const char *rp_last_error(void);

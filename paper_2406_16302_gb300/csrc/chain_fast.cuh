@@ -1,0 +1,364 @@
+// Evaluation of every base path of a root for edits without motion (and the
+// primal), from running products along the root's walks -- the cumulative
+// forward/backward pdf tables of Sec. 4.3 -- with O(1) work per path.
+//
+// Notation (p(a | b, c): area density of a sampled at c conditioned on b;
+// rho(a, b, c): BSDF at b with camera-side neighbour a and light-side
+// neighbour c).  Eye-side walk z_1 .. z_nz with z_0 = x_D; light-side walk
+// y_1 .. y_ny with y_0 = x_D; a path of technique (3) is
+// (camera, z_t .. z_1, x_D, y_1 .. y_s, L_s).  Per frame:
+//   E(t)    = W_e G(cam, z_t) rho(cam, z_t, z_t-1) G(z_t, z_t-1)
+//             prod_{m<t} rho(z_m+1, z_m, z_m-1) G(z_m, z_m-1)
+//   Pf(t)   = prod_{m<t} p(z_m-1 | z_m+1, z_m)          (toward the light)
+//   Pz(t)   = prod_{m<t} p(z_m+1 | z_m-1, z_m)          (toward the camera)
+//   Sz(t)   = sum_{m<t, z_m dynamic} pcos(z_m) Pf(m) prod_{m<=m'<t} p(z_m'+1 | z_m'-1, z_m')
+//   A(t)    = [7] p_cam(z_t) p(z_t-1 | cam, z_t) Pf(t)
+//           + [2][z_t dynamic] pD p(z_t-1 | cam, z_t) Pf(t) + [3] pD Sz(t)
+//   Ly(s)   = prod_{m<s} rho(y_m-1, y_m, y_m+1) G(y_m, y_m+1) rho(y_s-1, y_s, L_s) G(y_s, L_s) L_e
+//   Py(s)   = prod_{m<s} p(y_m+1 | y_m-1, y_m)
+//   PLy(m)  = prod_{m''<=m} p(y_m''-1 | y_m''+1, y_m'')
+//   Sy(s)   = sum_{m<s, y_m dynamic} pcos(y_m) PLy(m) prod_{m<m'<s} p(y_m'+1 | y_m'-1, y_m')
+//   B(s)    = [3] pD pcos(x_D) Py(s) + [1][y_s dynamic] pD PLy(s-1) p(y_s-1 | L_s, y_s) + [3] pD Sy(s)
+// and with the x_D factors rho_D = rho(z_1, x_D, y_1), pE_D = p(y_1 | z_1, x_D),
+// pL_D = p(z_1 | y_1, x_D):
+//   f(t, s) = E(t) rho_D G(x_D, y_1) Ly(s)
+//   P(t, s) = p_L (pE_D Py(s) A(t) + pL_D Pz(t) B(s))
+// where [n] marks the terms of technique n (balance heuristic over the
+// enabled techniques: path tracing [7] and one dynamic-vertex technique per
+// vertex on the edited object, Sec. 4.3).  Techniques (1), (2) and path
+// tracing are the same construction with one side fixed.  Both frames are
+// evaluated (they differ only at vertices on the edited object).
+#pragma once
+
+#include "chain_eval.cuh"
+#include "rp_device.cuh"
+
+namespace rp {
+
+namespace fast_detail {
+
+constexpr int kSide = kMaxDepth;   // walk vertices per side (bound)
+
+// frame-independent geometry of the camera connection of v
+struct CamTerm {
+    int pix;
+    float we;      // W_e G(cam, v), 0 if not in the image or facing away
+    float pcam;    // area density of v for a camera ray
+};
+
+__device__ __forceinline__ CamTerm cam_term(const DevScene &S, const Vtx &cam, const Vtx &v) {
+    CamTerm c;
+    float cc;
+    c.pix = camera_project(S, v.p, cc);
+    float3 d01 = cam.p - v.p;
+    float r2 = dot3(d01, d01);
+    float c1 = dot3(v.n, d01) / sqrtf(r2);
+    if (c.pix < 0 || c1 <= 0.f) {
+        c.we = 0.f;
+        c.pcam = 0.f;
+    } else {
+        c.we = c1 / r2 / (S.pix_area * cc * cc * cc);
+        c.pcam = c1 / r2 / (S.film_area * cc * cc * cc);
+    }
+    return c;
+}
+
+// eye side: for t = 1..nz with a camera connection, E(t) and A(t), Pz(t)
+struct Eye {
+    float3 E[2][kSide];
+    float A[2][kSide], Pz[2][kSide];
+    int pix[kSide];
+};
+
+// light side: for s = 1..ny with a next-event vertex, Ly(s), Py(s), B(s)
+struct Light {
+    float3 L[2][kSide];
+    float Py[2][kSide], B[2][kSide];
+};
+
+}  // namespace fast_detail
+
+// splat one no-motion path (fx, Pg: base frame; fy, Py: other frame)
+__device__ __forceinline__ void emit_nomotion(Ctx &cx, PathCounts &pc, uint32_t root, int tech,
+                                              int sa, int sb, int pa, float3 fx, float Pg,
+                                              float3 fy, float Py) {
+    const LaunchArgs &A = cx.A;
+    if (zero3(fx)) return;
+    ++pc.paths;
+    const float invN = A.invN;
+    if (!A.residual) {            // primal: a single frame, path tracing alone
+        emit(cx, root, tech, A.frame, sa, sb, pa, fx * (invN / Pg), -1, f3(0, 0, 0), 0, Pg, 0.f, 1.f);
+        return;
+    }
+    const float sign = (A.frame == 2) ? 1.0f : -1.0f;
+    if (!zero3(fy) && Py > 0.f) {
+        ++pc.accepted;
+        const float den = (Pg + Py) / invN;
+        const float3 va = fx * (sign / den), vb = fy * (-sign / den);
+        if (A.rec_count) {
+            emit(cx, root, tech, A.frame, sa, sb, pa, va, pa, vb, MAP_ACCEPT, Pg, Py, 1.0f);
+        } else if (A.img) {
+            splat(A.img, pa, va + vb);    // both splats land on one pixel
+        }
+    } else {
+        emit(cx, root, tech, A.frame, sa, sb, pa, fx * (sign * invN / Pg), -1, f3(0, 0, 0),
+             MAP_INVALID, Pg, 0.f, 0.f);
+    }
+}
+
+// eye side from x_D = z[0] (techniques (1) and (3))
+__device__ void fast_eye(const Ctx &cx, int nf, const int *frames, const Vtx *z, int nz,
+                         uint32_t cam, int mask, fast_detail::Eye &S) {
+    using namespace chain_detail;
+    using namespace fast_detail;
+    const DevScene &Sc = cx.A.S;
+    const Vtx camv = camera_vertex(cx);
+    const float pD = 1.0f / Sc.dyn_area;
+    for (int f = 0; f < nf; ++f) {
+        float3 prho = f3(1.f, 1.f, 1.f);
+        float Pf = 1.f, Pz = 1.f, Sz = 0.f;
+        for (int m = 1; m <= nz; ++m) {
+            const Vtx &zm = z[m], &zp = z[m - 1];
+            const Mat mm = get_mat(cx, frames[f], zm.mat);
+            const float G = G2(zm, zp);
+            const bool dyn = is_dyn(cx, zm);
+            if (cam & (1u << m)) {
+                const CamTerm ct = cam_term(Sc, camv, zm);
+                if (f == 0) S.pix[m] = ct.pix;
+                const float pEC = pdf3(mm, camv, zm, zp);
+                S.E[f][m] = mul3(prho, rho3(mm, camv, zm, zp)) * (ct.we * G);
+                S.A[f][m] = ((mask & 8) ? ct.pcam * pEC * Pf : 0.f) +
+                            ((mask & 2) && dyn ? pD * pEC * Pf : 0.f) + ((mask & 4) ? pD * Sz : 0.f);
+                S.Pz[f][m] = Pz;
+            }
+            if (m < nz) {
+                const Vtx &zn = z[m + 1];
+                const float pLI = pdf3(mm, zp, zm, zn);
+                if (dyn)
+                    Sz += area_from_dir(cosine_pdf(zm.n, unit3(zp.p - zm.p)), zm.p, zp) * Pf;
+                Sz *= pLI;
+                prho = mul3(prho, rho3(mm, zn, zm, zp)) * G;
+                Pf *= pdf3(mm, zn, zm, zp);
+                Pz *= pLI;
+            }
+        }
+    }
+}
+
+// light side from x_D = y[0] (techniques (2) and (3)); `with_dcos` adds the
+// technique-(3) term of x_D itself (pD pcos(x_D) Py)
+__device__ void fast_light(const Ctx &cx, int nf, const int *frames, const Vtx *y, const Vtx *L,
+                           int ny, uint32_t nee, int mask, float pcosD, fast_detail::Light &S) {
+    using namespace chain_detail;
+    using namespace fast_detail;
+    const DevScene &Sc = cx.A.S;
+    const float pD = 1.0f / Sc.dyn_area;
+    for (int f = 0; f < nf; ++f) {
+        float3 prho = f3(1.f, 1.f, 1.f);
+        float Py = 1.f, PLy = 1.f, Sy = 0.f;
+        for (int m = 1; m <= ny; ++m) {
+            const Vtx &ym = y[m], &yp = y[m - 1];
+            const Mat mm = get_mat(cx, frames[f], ym.mat);
+            const bool dyn = is_dyn(cx, ym);
+            if (nee & (1u << m)) {
+                S.L[f][m] = mul3(mul3(prho, rho3(mm, yp, ym, L[m])) * G2(ym, L[m]),
+                                 get_mat(cx, frames[f], L[m].mat).em);
+                S.Py[f][m] = Py;
+                const float pLL = pdf3(mm, L[m], ym, yp);
+                S.B[f][m] = ((mask & 4) ? pD * (pcosD * Py + Sy) : 0.f) +
+                            ((mask & 1) && dyn ? pD * PLy * pLL : 0.f);
+            }
+            if (m < ny) {
+                const Vtx &yn = y[m + 1];
+                const float pLI = pdf3(mm, yn, ym, yp);
+                const float pEI = pdf3(mm, yp, ym, yn);
+                PLy *= pLI;
+                Sy *= pEI;
+                if (dyn) Sy += area_from_dir(cosine_pdf(ym.n, unit3(yn.p - ym.p)), ym.p, yn) * PLy;
+                prho = mul3(prho, rho3(mm, yp, ym, yn)) * G2(ym, yn);
+                Py *= pEI;
+            }
+        }
+    }
+}
+
+// technique (3): all (t, s) paths of one root
+__device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *z, int nz, uint32_t cam,
+                        const Vtx *y, const Vtx *L, int ny, uint32_t nee) {
+    using namespace chain_detail;
+    const LaunchArgs &A = cx.A;
+    const int g = A.frame, D = A.S.max_depth, mask = A.tech_mask;
+    const int frames[2] = {g, 3 - g};
+    const float pLi = 1.0f / A.S.emit_area;
+    const Vtx &xD = z[0];
+    const float pcosD = area_from_dir(cosine_pdf(xD.n, unit3(y[1].p - xD.p)), xD.p, y[1]);
+    fast_detail::Eye ze;
+    fast_detail::Light yl;
+    fast_eye(cx, 2, frames, z, nz, cam, mask, ze);
+    fast_light(cx, 2, frames, y, L, ny, nee, mask, pcosD, yl);
+    const float Gd = G2(xD, y[1]);
+    float3 rD[2];
+    float pE[2], pL[2];
+    for (int f = 0; f < 2; ++f) {
+        const Mat m = get_mat(cx, frames[f], xD.mat);
+        rD[f] = rho3(m, z[1], xD, y[1]) * Gd;
+        pE[f] = pdf3(m, z[1], xD, y[1]);
+        pL[f] = pdf3(m, y[1], xD, z[1]);
+    }
+    for (int t = 1; t <= nz; ++t) {
+        if (!(cam & (1u << t))) continue;
+        for (int s = 1; s <= ny && t + s <= D - 2; ++s) {
+            if (!(nee & (1u << s))) continue;
+            float3 fv[2];
+            float P[2];
+            for (int f = 0; f < 2; ++f) {
+                fv[f] = mul3(mul3(ze.E[f][t], rD[f]), yl.L[f][s]);
+                P[f] = pLi * (pE[f] * yl.Py[f][s] * ze.A[f][t] + pL[f] * ze.Pz[f][t] * yl.B[f][s]);
+            }
+            emit_nomotion(cx, pc, root, T_3, t, s, ze.pix[t], fv[0], P[0], fv[1], P[1]);
+        }
+    }
+}
+
+// technique (1): paths (camera, z_t .. z_1, x_D, x_L), t = 0 .. nz
+__device__ void fast_t1(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *z, int nz, uint32_t cam,
+                        const Vtx &xL) {
+    using namespace chain_detail;
+    const LaunchArgs &A = cx.A;
+    const DevScene &Sc = A.S;
+    const int g = A.frame, mask = A.tech_mask;
+    const int frames[2] = {g, 3 - g};
+    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
+    const Vtx &xD = z[0];
+    const float3 Le = get_mat(cx, g, xL.mat).em * G2(xD, xL);
+    const Vtx camv = camera_vertex(cx);
+    if (cam & 1u) {                              // t = 0: (camera, x_D, x_L)
+        const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, xD);
+        if (ct.we > 0.f) {
+            const float P = pLi * (((mask & 8) ? ct.pcam : 0.f) + ((mask & 1) ? pD : 0.f));
+            const float3 base = Le * ct.we;
+            emit_nomotion(cx, pc, root, T_1, 0, 0, ct.pix,
+                          mul3(base, rho3(get_mat(cx, frames[0], xD.mat), camv, xD, xL)), P,
+                          mul3(base, rho3(get_mat(cx, frames[1], xD.mat), camv, xD, xL)), P);
+        }
+    }
+    if (nz == 0) return;
+    fast_detail::Eye ze;
+    fast_eye(cx, 2, frames, z, nz, cam, mask, ze);
+    float3 rD[2];
+    float pLL[2];
+    for (int f = 0; f < 2; ++f) {
+        const Mat m = get_mat(cx, frames[f], xD.mat);
+        rD[f] = mul3(rho3(m, z[1], xD, xL), Le);
+        pLL[f] = pdf3(m, xL, xD, z[1]);
+    }
+    for (int t = 1; t <= nz; ++t) {
+        if (!(cam & (1u << t))) continue;
+        float3 fv[2];
+        float P[2];
+        for (int f = 0; f < 2; ++f) {
+            fv[f] = mul3(ze.E[f][t], rD[f]);
+            P[f] = pLi * (ze.A[f][t] + ((mask & 1) ? pD * ze.Pz[f][t] * pLL[f] : 0.f));
+        }
+        emit_nomotion(cx, pc, root, T_1, t, 0, ze.pix[t], fv[0], P[0], fv[1], P[1]);
+    }
+}
+
+// technique (2): paths (camera, x_D, y_1 .. y_s, L_s), s = 1 .. ny
+__device__ void fast_t2(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *y, const Vtx *L, int ny,
+                        uint32_t nee) {
+    using namespace chain_detail;
+    const LaunchArgs &A = cx.A;
+    const DevScene &Sc = A.S;
+    const int g = A.frame, mask = A.tech_mask;
+    const int frames[2] = {g, 3 - g};
+    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
+    const Vtx &xD = y[0];
+    const Vtx camv = camera_vertex(cx);
+    const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, xD);
+    if (ct.we <= 0.f) return;
+    fast_detail::Light yl;
+    // x_D is technique (2) here: no technique-(3) term at x_D
+    fast_light(cx, 2, frames, y, L, ny, nee, mask, 0.f, yl);
+    const float Gd = G2(xD, y[1]);
+    const float a = ((mask & 8) ? ct.pcam : 0.f) + ((mask & 2) ? pD : 0.f);
+    float3 rD[2];
+    float pEC[2];
+    for (int f = 0; f < 2; ++f) {
+        const Mat m = get_mat(cx, frames[f], xD.mat);
+        rD[f] = rho3(m, camv, xD, y[1]) * (ct.we * Gd);
+        pEC[f] = pdf3(m, camv, xD, y[1]);
+    }
+    for (int s = 1; s <= ny; ++s) {
+        if (!(nee & (1u << s))) continue;
+        float3 fv[2];
+        float P[2];
+        for (int f = 0; f < 2; ++f) {
+            fv[f] = mul3(rD[f], yl.L[f][s]);
+            P[f] = pLi * (a * pEC[f] * yl.Py[f][s] + yl.B[f][s]);
+        }
+        emit_nomotion(cx, pc, root, T_2, 0, s, ct.pix, fv[0], P[0], fv[1], P[1]);
+    }
+}
+
+// path tracing: paths (camera, x_1 .. x_j, L_j); residual (technique (7),
+// both frames, static paths skipped) or primal (one frame, path tracing only)
+__device__ void fast_pt(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *x, const Vtx *L, int len,
+                        uint32_t nee, int tech) {
+    using namespace chain_detail;
+    const LaunchArgs &A = cx.A;
+    const DevScene &Sc = A.S;
+    const int g = A.frame;
+    const bool res = A.residual != 0;
+    const int mask = res ? A.tech_mask : 8;
+    const int nf = res ? 2 : 1;
+    const int frames[2] = {g, 3 - g};
+    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
+    const Vtx camv = camera_vertex(cx);
+    const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, x[1]);
+    if (ct.we <= 0.f) return;
+    if (!res) {                    // the camera ray sees an emitter: (camera, x_1)
+        const float3 em = get_mat(cx, g, x[1].mat).em;
+        if (!zero3(em)) emit_nomotion(cx, pc, root, tech, 0, 2, ct.pix, em * ct.we, ct.pcam, em, 0.f);
+    }
+    const bool d1 = is_dyn(cx, x[1]);
+    float3 R[2] = {f3(ct.we, ct.we, ct.we), f3(ct.we, ct.we, ct.we)};
+    float PE[2] = {1.f, 1.f}, PL[2] = {1.f, 1.f}, S3[2] = {0.f, 0.f};
+    bool any_dyn = false;
+    for (int j = 1; j <= len; ++j) {
+        const Vtx &xj = x[j];
+        const Vtx &xp = (j == 1) ? camv : x[j - 1];
+        const bool dj = is_dyn(cx, xj);
+        any_dyn = any_dyn || dj;
+        if ((nee & (1u << j)) && (!res || any_dyn)) {
+            const float GL = G2(xj, L[j]);
+            float3 fv[2];
+            float P[2] = {0.f, 0.f};
+            for (int f = 0; f < nf; ++f) {
+                const Mat m = get_mat(cx, frames[f], xj.mat);
+                fv[f] = mul3(mul3(R[f], rho3(m, xp, xj, L[j])) * GL, get_mat(cx, frames[f], L[j].mat).em);
+                float p = ((mask & 8) ? ct.pcam * PE[f] : 0.f) +
+                          ((mask & 2) && d1 && j >= 2 ? pD * PE[f] : 0.f) + ((mask & 4) ? pD * S3[f] : 0.f);
+                if ((mask & 1) && dj) p += pD * (j == 1 ? 1.f : PL[f] * pdf3(m, L[j], xj, xp));
+                P[f] = pLi * p;
+            }
+            emit_nomotion(cx, pc, root, tech, 0, j + 2, ct.pix, fv[0], P[0], fv[1], P[1]);
+        }
+        if (j < len) {
+            const Vtx &xn = x[j + 1];
+            for (int f = 0; f < nf; ++f) {
+                const Mat m = get_mat(cx, frames[f], xj.mat);
+                const float pE = pdf3(m, xp, xj, xn);
+                R[f] = mul3(R[f], rho3(m, xp, xj, xn)) * G2(xj, xn);
+                S3[f] *= pE;
+                if (j >= 2) {
+                    PL[f] *= pdf3(m, xn, xj, xp);
+                    if (dj) S3[f] += area_from_dir(cosine_pdf(xj.n, unit3(xn.p - xj.p)), xj.p, xn) * PL[f];
+                }
+                PE[f] *= pE;
+            }
+        }
+    }
+}
+
+}  // namespace rp

@@ -18,7 +18,7 @@
 // the same samples.
 #include <cooperative_groups.h>
 
-#include "chain_eval.cuh"
+#include "chain_fast.cuh"
 #include "rp_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
 }
 
 // closest hits of a queue
-__global__ void __launch_bounds__(kBlock) k_trace_closest(const __grid_constant__ LaunchArgs A, int it) {
+__global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_trace_closest(const __grid_constant__ LaunchArgs A, int it) {
     __shared__ int s_stack[kStackDepth * kBlock];
     Ctx c(A, s_stack + threadIdx.x);
     const WaveBuf &W = A.W;
@@ -280,11 +280,13 @@ __global__ void __launch_bounds__(kBlock) k_trace_closest(const __grid_constant_
         add_stat(A.stats, ST_RAYS_CLOSEST, c.cnt.rays_closest);
         add_stat(A.stats, ST_NODES, c.cnt.nodes);
         add_stat(A.stats, ST_TRIS, c.cnt.tris);
+        add_stat(A.stats, ST_NODES_C, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS_C, c.cnt.tris);
     }
 }
 
 // shadow rays: visibility of connections, or ghost crossings of edges
-__global__ void __launch_bounds__(kBlock) k_trace_shadow(const __grid_constant__ LaunchArgs A, int it) {
+__global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_trace_shadow(const __grid_constant__ LaunchArgs A, int it) {
     __shared__ int s_stack[kStackDepth * kBlock];
     Ctx c(A, s_stack + threadIdx.x);
     const WaveBuf &W = A.W;
@@ -310,6 +312,8 @@ __global__ void __launch_bounds__(kBlock) k_trace_shadow(const __grid_constant__
         add_stat(A.stats, ST_RAYS_SHADOW, c.cnt.rays_shadow);
         add_stat(A.stats, ST_NODES, c.cnt.nodes);
         add_stat(A.stats, ST_TRIS, c.cnt.tris);
+        add_stat(A.stats, ST_NODES_S, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS_S, c.cnt.tris);
     }
 }
 
@@ -365,157 +369,110 @@ __device__ int assemble(const Ctx &c, uint32_t r, int tech, int sa, int sb, Vtx 
 
 }  // namespace
 
+// motion: every non-static base path of a root becomes a mapping task
 template <int T>
-__global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs A) {
+__global__ void __launch_bounds__(128) k_enum(const __grid_constant__ LaunchArgs A) {
+    const uint32_t n = A.root_end - A.root_begin;
+    const WaveBuf &W = A.W;
+    Ctx c(A, nullptr);
+    PathCounts pc{0, 0, 0};
+    const int D = A.S.max_depth;
+    const int g = A.frame;
+    Vtx x[1];
+    unsigned int roots = 0;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        ++roots;
+        const uint32_t cam = W.cam_ok[r], nee = W.nee_ok[r];
+        // enumerate the non-static base paths into mapping tasks
+        if (T == T_1) {
+            if (!(W.flags[r] & RF_ROOT_OK)) continue;
+            for (int t = 0; t <= W.len_eye[r]; ++t)
+                if (cam & (1u << t)) dispatch_path(c, pc, x, 0, r, T_1, t, 0);
+        } else if (T == T_2) {
+            if (!(W.flags[r] & RF_ROOT_OK)) continue;
+            for (int s2 = 1; s2 <= W.len_light[r]; ++s2)
+                if (nee & (1u << s2)) dispatch_path(c, pc, x, 0, r, T_2, 0, s2);
+        } else if (T == T_3) {
+            const int nz = W.len_eye[r], ny = W.len_light[r];
+            for (int te = 1; te <= nz; ++te) {
+                if (!(cam & (1u << te))) continue;
+                for (int sl = 1; sl <= ny && te + sl <= D - 2; ++sl)
+                    if (nee & (1u << sl)) dispatch_path(c, pc, x, 0, r, T_3, te, sl);
+            }
+        } else {
+            const int len = W.len_light[r];
+            if (len == 0) continue;
+            const uint32_t gw = W.ghost_w[r], gn = W.ghost_n[r];
+            unsigned dynmask = 0u;
+            for (int j = 1; j <= len; ++j) {
+                const int prim = W.prim[(size_t)(j == 1 ? 0 : slot_light(D, j - 1)) * W.R + r];
+                if (prim >= A.S.n_static) dynmask |= 1u << j;
+            }
+            const Vtx x1 = load_vtx(c, W, 0, r);
+            if (!zero3(get_mat(c, g, x1.mat).em) && ((dynmask & 2u) || (gw & 2u)))
+                dispatch_path(c, pc, x, 0, r, T_7, 0, 2);
+            for (int j = 1; j <= len; ++j) {
+                if (!(nee & (1u << j))) continue;
+                const unsigned upto = (2u << j) - 2u;
+                if ((dynmask & upto) || (gw & upto) || (gn & (1u << j)))
+                    dispatch_path(c, pc, x, 0, r, T_7, 0, j + 2);
+            }
+        }
+    }
+    if (A.stats) add_stat(A.stats, ST_ROOTS, roots);
+}
+
+// edits without motion, and the primal: every base path of a root from
+// running products along its walks (chain_fast.cuh), O(1) work per path
+template <int T>
+__global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ LaunchArgs A) {
     const uint32_t n = A.root_end - A.root_begin;
     const WaveBuf &W = A.W;
     Ctx c(A, nullptr);
     PathCounts pc{0, 0, 0};
     unsigned int roots = 0;
     const int D = A.S.max_depth;
-    const int g = A.frame;
-    const bool motion = A.residual && A.E.motion;
-    Vtx ch[kChain], L[kChain], x[kMaxVerts];
-    ChainTables tb;
+    Vtx zv[kMaxDepth + 1], yv[kMaxDepth + 1], Lv[kMaxDepth + 1];
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         ++roots;
         const uint32_t root = A.root_begin + r;
         const uint32_t cam = W.cam_ok[r], nee = W.nee_ok[r];
-        if (motion) {
-            // enumerate the non-static base paths into mapping tasks
-            if (T == T_1) {
-                if (!(W.flags[r] & RF_ROOT_OK)) continue;
-                for (int t = 0; t <= W.len_eye[r]; ++t)
-                    if (cam & (1u << t)) dispatch_path(c, pc, x, 0, r, T_1, t, 0);
-            } else if (T == T_2) {
-                if (!(W.flags[r] & RF_ROOT_OK)) continue;
-                for (int s2 = 1; s2 <= W.len_light[r]; ++s2)
-                    if (nee & (1u << s2)) dispatch_path(c, pc, x, 0, r, T_2, 0, s2);
-            } else if (T == T_3) {
-                const int nz = W.len_eye[r], ny = W.len_light[r];
-                for (int te = 1; te <= nz; ++te) {
-                    if (!(cam & (1u << te))) continue;
-                    for (int sl = 1; sl <= ny && te + sl <= D - 2; ++sl)
-                        if (nee & (1u << sl)) dispatch_path(c, pc, x, 0, r, T_3, te, sl);
-                }
-            } else {
-                const int len = W.len_light[r];
-                if (len == 0) continue;
-                const uint32_t gw = W.ghost_w[r], gn = W.ghost_n[r];
-                unsigned dynmask = 0u;
-                for (int j = 1; j <= len; ++j) {
-                    const int prim = W.prim[(size_t)(j == 1 ? 0 : slot_light(D, j - 1)) * W.R + r];
-                    if (prim >= A.S.n_static) dynmask |= 1u << j;
-                }
-                const Vtx x1 = load_vtx(c, W, 0, r);
-                if (!zero3(get_mat(c, g, x1.mat).em) && ((dynmask & 2u) || (gw & 2u)))
-                    dispatch_path(c, pc, x, 0, r, T_7, 0, 2);
-                for (int j = 1; j <= len; ++j) {
-                    if (!(nee & (1u << j))) continue;
-                    const unsigned upto = (2u << j) - 2u;
-                    if ((dynmask & upto) || (gw & upto) || (gn & (1u << j)))
-                        dispatch_path(c, pc, x, 0, r, T_7, 0, j + 2);
-                }
-            }
-            continue;
-        }
-        // no motion (or primal): build the chain, its tables, and evaluate every path
-        int M = 0;
-        unsigned ce = 0u, le = 0u;
-        if (T == T_1) {
-            if (!(W.flags[r] & RF_ROOT_OK)) continue;
-            const int nz = W.len_eye[r];
-            for (int i = 0; i < nz; ++i) {
-                ch[i] = load_vtx(c, W, slot_eye(D, nz - i), r);
-                if (cam & (1u << (nz - i))) ce |= 1u << i;
-            }
-            ch[nz] = load_vtx(c, W, 0, r);
-            if (cam & 1u) ce |= 1u << nz;
-            L[nz] = load_vtx(c, W, 1, r);
-            le = 1u << nz;
-            M = nz + 1;
-        } else if (T == T_2) {
-            if (!(W.flags[r] & RF_ROOT_OK)) continue;
-            const int ny = W.len_light[r];
-            ch[0] = load_vtx(c, W, 0, r);
-            ce = 1u;
-            for (int m = 1; m <= ny; ++m) {
-                ch[m] = load_vtx(c, W, slot_light(D, m), r);
-                if (nee & (1u << m)) {
-                    le |= 1u << m;
-                    L[m] = load_vtx(c, W, slot_nee(D, m), r);
-                }
-            }
-            M = ny + 1;
-        } else if (T == T_3) {
-            const int nz = W.len_eye[r], ny = W.len_light[r];
-            if (nz == 0 || ny == 0) continue;
-            for (int i = 0; i < nz; ++i) {
-                ch[i] = load_vtx(c, W, slot_eye(D, nz - i), r);
-                if (cam & (1u << (nz - i))) ce |= 1u << i;
-            }
-            ch[nz] = load_vtx(c, W, 0, r);
-            for (int m = 1; m <= ny; ++m) {
-                ch[nz + m] = load_vtx(c, W, slot_light(D, m), r);
-                if (nee & (1u << m)) {
-                    le |= 1u << (nz + m);
-                    L[nz + m] = load_vtx(c, W, slot_nee(D, m), r);
-                }
-            }
-            M = nz + ny + 1;
-        } else {
+        if (T == T_PT) {
             const int len = W.len_light[r];
             if (len == 0) continue;
+            if (A.residual) {
+                // without motion only paths through the edited object contribute
+                bool any_dyn = false;
+                for (int j = 1; j <= len && !any_dyn; ++j)
+                    any_dyn = W.prim[(size_t)(j == 1 ? 0 : slot_light(D, j - 1)) * W.R + r] >= A.S.n_static;
+                if (!any_dyn) continue;
+            }
             for (int j = 1; j <= len; ++j) {
-                ch[j - 1] = load_vtx(c, W, j == 1 ? 0 : slot_light(D, j - 1), r);
-                if (nee & (1u << j)) {
-                    le |= 1u << (j - 1);
-                    L[j - 1] = load_vtx(c, W, slot_nee(D, j), r);
-                }
+                yv[j] = load_vtx(c, W, j == 1 ? 0 : slot_light(D, j - 1), r);
+                if (nee & (1u << j)) Lv[j] = load_vtx(c, W, slot_nee(D, j), r);
             }
-            ce = 1u;
-            M = len;
+            fast_pt(c, pc, root, yv, Lv, len, nee, A.residual ? T_7 : T_PT);
+            continue;
         }
-        build_tables(c, g, 3 - g, A.residual != 0, ch, L, M, ce, le, tb);
-        if (T == T_1) {
-            const int nz = M - 1;
-            for (int t = 0; t <= nz; ++t)
-                if (ce & (1u << (nz - t))) chain_emit(c, pc, tb, nz - t, nz, root, T_1, t, 0);
-        } else if (T == T_2) {
-            for (int s2 = 1; s2 < M; ++s2)
-                if (le & (1u << s2)) chain_emit(c, pc, tb, 0, s2, root, T_2, 0, s2);
-        } else if (T == T_3) {
-            const int nz = W.len_eye[r], ny = W.len_light[r];
-            for (int te = 1; te <= nz; ++te) {
-                if (!(ce & (1u << (nz - te)))) continue;
-                for (int sl = 1; sl <= ny && te + sl <= D - 2; ++sl)
-                    if (le & (1u << (nz + sl)))
-                        chain_emit(c, pc, tb, nz - te, nz + sl, root, T_3, te, sl);
-            }
-        } else {
-            const int tech = A.residual ? T_7 : T_PT;
-            if (!A.residual) {
-                // the camera ray sees an emitter: path (camera, x_1)
-                const float3 em = get_mat(c, g, ch[0].mat).em;
-                if (!zero3(em) && tb.WeG0[0] > 0.f) {
-                    ++pc.paths;
-                    emit(c, root, tech, g, 0, 2, tb.pix[0], em * (tb.WeG0[0] * A.invN / tb.pcam[0]),
-                         -1, f3(0, 0, 0), 0, tb.pcam[0], 0.f, 1.f);
-                }
-            }
-            for (int j = 1; j <= M; ++j) {
-                if (!(le & (1u << (j - 1)))) continue;
-                // without motion a path is static when no vertex lies on the object
-                if (A.residual && !(tb.dyn & ((1u << j) - 1u))) continue;
-                chain_emit(c, pc, tb, 0, j - 1, root, tech, 0, j + 2);
-            }
+        if ((T == T_1 || T == T_2) && !(W.flags[r] & RF_ROOT_OK)) continue;
+        const int nz = (T == T_2) ? 0 : W.len_eye[r];
+        const int ny = (T == T_1) ? 0 : W.len_light[r];
+        if (T == T_3 && (nz == 0 || ny == 0)) continue;
+        zv[0] = load_vtx(c, W, 0, r);
+        for (int m = 1; m <= nz; ++m) zv[m] = load_vtx(c, W, slot_eye(D, m), r);
+        yv[0] = zv[0];
+        for (int m = 1; m <= ny; ++m) {
+            yv[m] = load_vtx(c, W, slot_light(D, m), r);
+            if (nee & (1u << m)) Lv[m] = load_vtx(c, W, slot_nee(D, m), r);
         }
+        if (T == T_1) fast_t1(c, pc, root, zv, nz, cam, load_vtx(c, W, 1, r));
+        else if (T == T_2) fast_t2(c, pc, root, yv, Lv, ny, nee);
+        else fast_t3(c, pc, root, zv, nz, cam, yv, Lv, ny, nee);
     }
     if (A.stats) {
         add_stat(A.stats, ST_ROOTS, roots);
         add_stat(A.stats, ST_PATHS, pc.paths);
         add_stat(A.stats, ST_ACCEPTED, pc.accepted);
-        add_stat(A.stats, ST_REJECTED, pc.rejected);
     }
 }
 
@@ -547,10 +504,53 @@ __global__ void __launch_bounds__(kBlock) k_map(const __grid_constant__ LaunchAr
 
 namespace {
 
+cudaEvent_t timer_event(KernelTimer *t) {
+    if (t->pool_used == t->pool_n) {
+        if (t->pool_n == t->pool_cap) {
+            int cap = t->pool_cap ? 2 * t->pool_cap : 256;
+            cudaEvent_t *p = new cudaEvent_t[cap];
+            for (int i = 0; i < t->pool_n; ++i) p[i] = t->pool[i];
+            delete[] t->pool;
+            t->pool = p;
+            t->pool_cap = cap;
+        }
+        cudaEventCreate(&t->pool[t->pool_n++]);
+    }
+    return t->pool[t->pool_used++];
+}
+
+void timer_begin(KernelTimer *t, cudaStream_t s, cudaEvent_t *e0, cudaEvent_t *e1) {
+    *e0 = timer_event(t);
+    *e1 = timer_event(t);
+    cudaEventRecord(*e0, s);
+}
+
+void timer_end(KernelTimer *t, const char *name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    cudaEventRecord(e1, s);
+    if (t->n == t->cap) {
+        int cap = t->cap ? 2 * t->cap : 256;
+        KernelTimer::Entry *p = new KernelTimer::Entry[cap];
+        for (int i = 0; i < t->n; ++i) p[i] = t->entries[i];
+        delete[] t->entries;
+        t->entries = p;
+        t->cap = cap;
+    }
+    t->entries[t->n++] = KernelTimer::Entry{name, e0, e1};
+}
+
 inline int grid_for(uint32_t n, int block, int cap) {
     uint32_t g = (n + block - 1) / block;
     return (int)(g < (uint32_t)cap ? (g > 0 ? g : 1) : cap);
 }
+
+// one launch, optionally bracketed by timing events
+#define RP_LAUNCH(name, grid, block, kernel, ...)                                    \
+    do {                                                                             \
+        cudaEvent_t e0_ = nullptr, e1_ = nullptr;                                    \
+        if (a.timer) timer_begin(a.timer, s, &e0_, &e1_);                           \
+        kernel<<<(grid), (block), 0, s>>>(__VA_ARGS__);                             \
+        if (a.timer) timer_end(a.timer, name, s, e0_, e1_);                         \
+    } while (0)
 
 template <int T>
 cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
@@ -560,24 +560,29 @@ cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
     const int gQ = 152 * 16;                 // persistent-style grids over device-side counts
     cudaError_t e = cudaMemsetAsync(a.W.counts, 0, sizeof(unsigned int) * kCountSlots, s);
     if (e != cudaSuccess) return e;
-    k_gen<T><<<gR, 256, 0, s>>>(a);
+    RP_LAUNCH("k_gen", gR, 256, k_gen<T>, a);
     int it0 = 1;
     if (T == T_1 || T == T_2) {
-        k_trace_shadow<<<gQ, kBlock, 0, s>>>(a, 0);
-        k_start<T><<<gR, 256, 0, s>>>(a);
-        k_trace_shadow<<<gQ, kBlock, 0, s>>>(a, 1);
+        RP_LAUNCH("k_trace_shadow", gQ, kBlock, k_trace_shadow, a, 0);
+        RP_LAUNCH("k_start", gR, 256, k_start<T>, a);
+        RP_LAUNCH("k_trace_shadow", gQ, kBlock, k_trace_shadow, a, 1);
         it0 = 1;
     }
     // iterations: closest rays pushed at iteration it-1 are traced, extended
     // into iteration it's rays, and the new shadow rays (slot it+1) traced
     const int iters = D + 1;
     for (int it = it0; it <= iters && it + 1 < kMaxIter; ++it) {
-        k_trace_closest<<<gQ, kBlock, 0, s>>>(a, it - 1);
-        k_extend<T><<<gQ, 256, 0, s>>>(a, it);
-        k_trace_shadow<<<gQ, kBlock, 0, s>>>(a, it + 1);
+        RP_LAUNCH("k_trace_closest", gQ, kBlock, k_trace_closest, a, it - 1);
+        RP_LAUNCH("k_extend", gQ, 256, k_extend<T>, a, it);
+        RP_LAUNCH("k_trace_shadow", gQ, kBlock, k_trace_shadow, a, it + 1);
     }
-    k_eval<T><<<grid_for(n, 128, 1 << 20), 128, 0, s>>>(a);
-    if (a.residual && a.E.motion) k_map<<<gQ, kBlock, 0, s>>>(a);
+    const int gE = grid_for(n, 128, 1 << 20);
+    if (a.residual && a.E.motion) {
+        RP_LAUNCH("k_enum", gE, 128, k_enum<T>, a);
+        RP_LAUNCH("k_map", gQ, kBlock, k_map, a);
+    } else {
+        RP_LAUNCH("k_eval", gE, 128, k_eval_fast<T>, a);
+    }
     return cudaGetLastError();
 }
 

@@ -69,6 +69,8 @@ struct rp_scene_s {
     std::vector<void *> wave_allocs;
     bool wave_tasks = false;
     uint32_t wave_cap = 1u << 22;  // roots per wave
+    KernelTimer timer;
+    bool timing_on = false;
     void free_wave() {
         for (void *p : wave_allocs) cudaFree(p);
         wave_allocs.clear();
@@ -80,6 +82,9 @@ struct rp_scene_s {
         if (d_stats) cudaFree(d_stats);
         if (d_scratch) cudaFree(d_scratch);
         free_wave();
+        for (int i = 0; i < timer.pool_n; ++i) cudaEventDestroy(timer.pool[i]);
+        delete[] timer.pool;
+        delete[] timer.entries;
     }
 };
 
@@ -361,6 +366,7 @@ static LaunchArgs base_args(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64
     a.tech_mask = (int)mask;
     a.stats = sc->stats_on ? sc->d_stats : nullptr;
     a.residual = 1;
+    a.timer = sc->timing_on ? &sc->timer : nullptr;
     return a;
 }
 
@@ -608,6 +614,42 @@ extern "C" rp_status rp_get_stats(rp_scene *scene, rp_stats *out) {
     out->tris_tested = h[ST_TRIS];
     out->accepted = h[ST_ACCEPTED];
     out->rejected = h[ST_REJECTED];
+    out->nodes_closest = h[ST_NODES_C];
+    out->tris_closest = h[ST_TRIS_C];
+    out->nodes_shadow = h[ST_NODES_S];
+    out->tris_shadow = h[ST_TRIS_S];
+    return RP_OK;
+}
+
+extern "C" rp_status rp_enable_timing(rp_scene *scene, int on) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    scene->timing_on = on != 0;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_get_kernel_times(rp_scene *scene, rp_kernel_time *out, int capacity,
+                                         int *count) {
+    if (!scene || !count || (capacity > 0 && !out)) return fail(RP_ERR_INVALID_ARG, "null argument");
+    KernelTimer &t = scene->timer;
+    RP_CUDA(cudaStreamSynchronize(scene->last_stream), "sync");
+    std::vector<rp_kernel_time> agg;
+    for (int i = 0; i < t.n; ++i) {
+        float ms = 0.f;
+        RP_CUDA(cudaEventElapsedTime(&ms, t.entries[i].start, t.entries[i].stop), "event time");
+        size_t j = 0;
+        while (j < agg.size() && std::strcmp(agg[j].name, t.entries[i].name) != 0) ++j;
+        if (j == agg.size()) {
+            rp_kernel_time k{};
+            std::strncpy(k.name, t.entries[i].name, sizeof(k.name) - 1);
+            agg.push_back(k);
+        }
+        agg[j].launches += 1;
+        agg[j].ms += ms;
+    }
+    t.n = 0;
+    t.pool_used = 0;
+    *count = (int)agg.size();
+    for (int i = 0; i < (int)agg.size() && i < capacity; ++i) out[i] = agg[i];
     return RP_OK;
 }
 

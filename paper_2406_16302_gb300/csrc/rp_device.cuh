@@ -22,6 +22,12 @@
 #ifndef RP_WALK_FP64
 #define RP_WALK_FP64 0
 #endif
+#ifndef RP_REFINE_FP64
+#define RP_REFINE_FP64 1
+#endif
+#ifndef RP_TRACE_MINBLOCKS
+#define RP_TRACE_MINBLOCKS 8
+#endif
 
 namespace rp {
 
@@ -540,6 +546,17 @@ static __device__ __forceinline__ Mat get_mat(const Ctx &c, int frame, int mat) 
 // (in object space for the dynamic object), position rounded once
 static __device__ void refine_hit(const Ctx &c, int g, float3 o, float3 d, Hit &h) {
     const DevScene &S = c.A.S;
+#if !RP_REFINE_FP64
+    {   // single precision: the point of the watertight barycentrics
+        const bool dynp = h.prim >= S.n_static;
+        const float4 *tr = dynp ? S.dyn_tri + 3 * (h.prim - S.n_static) : S.stat_tri + 3 * h.prim;
+        const float3 v0 = xyz(tr[0]);
+        float3 p = v0 + (xyz(tr[1]) - v0) * h.b1 + (xyz(tr[2]) - v0) * h.b2;
+        if (dynp) p = affine(c.A.E.M[g], p);
+        h.p = p;
+        return;
+    }
+#endif
     const bool dyn = h.prim >= S.n_static;
     const float4 *tri = dyn ? S.dyn_tri + 3 * (h.prim - S.n_static) : S.stat_tri + 3 * h.prim;
     double3 od = d3(o), dd = d3(d);

@@ -70,8 +70,21 @@ struct Record {
 
 enum StatIndex {
     ST_ROOTS = 0, ST_PATHS, ST_RAYS_CLOSEST, ST_RAYS_SHADOW, ST_NODES, ST_TRIS,
-    ST_ACCEPTED, ST_REJECTED, ST_COUNT
+    ST_ACCEPTED, ST_REJECTED, ST_NODES_C, ST_TRIS_C, ST_NODES_S, ST_TRIS_S, ST_COUNT
 };
+
+// host-side record of kernel launches bracketed by events (per-kernel timing)
+struct KernelTimer {
+    struct Entry {
+        const char *name;
+        cudaEvent_t start, stop;
+    };
+    Entry *entries = nullptr;
+    int n = 0, cap = 0;
+    cudaEvent_t *pool = nullptr;
+    int pool_n = 0, pool_cap = 0, pool_used = 0;
+};
+
 
 struct LaunchArgs {
     DevScene S;
@@ -88,6 +101,7 @@ struct LaunchArgs {
     unsigned long long *stats;  // ST_COUNT counters or null
     WaveBuf W;                  // wavefront buffers (wavefront mode)
     int residual;               // 1: residual techniques, 0: primal path tracing
+    KernelTimer *timer;         // host only: per-kernel event timing, or null
 };
 
 // launchers implemented in the .cu files

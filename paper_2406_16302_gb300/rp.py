@@ -48,7 +48,12 @@ class rp_edit_desc(C.Structure):
 class rp_stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("roots", "paths", "rays_closest", "rays_shadow",
                                               "nodes_visited", "tris_tested", "accepted",
-                                              "rejected")]
+                                              "rejected", "nodes_closest", "tris_closest",
+                                              "nodes_shadow", "tris_shadow")]
+
+
+class rp_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_ulonglong), ("ms", C.c_double)]
 
 
 RECORD_DTYPE = np.dtype([
@@ -61,7 +66,8 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
            "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_f32_noalloc",
            "rp_render_residual_host",
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
-           "rp_enable_stats", "rp_get_stats", "rp_last_error"]
+           "rp_enable_stats", "rp_get_stats", "rp_enable_timing", "rp_get_kernel_times",
+           "rp_last_error"]
 
 _lib = None
 
@@ -91,6 +97,8 @@ def lib():
         "rp_philox": (I, [U32, P, P, P, P]),
         "rp_enable_stats": (I, [P, I]),
         "rp_get_stats": (I, [P, P]),
+        "rp_enable_timing": (I, [P, I]),
+        "rp_get_kernel_times": (I, [P, P, I, P]),
         "rp_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -261,6 +269,20 @@ def rp_get_stats(scene: Scene) -> dict:
     s = rp_stats()
     _check(lib().rp_get_stats(scene.h, C.byref(s)))
     return {n: int(getattr(s, n)) for n, _ in rp_stats._fields_}
+
+
+def rp_enable_timing(scene: Scene, on=True):
+    _check(lib().rp_enable_timing(scene.h, 1 if on else 0))
+
+
+def rp_get_kernel_times(scene: Scene) -> dict:
+    """{kernel name: (launches, total ms)} since the previous call."""
+    cap = 64
+    arr = (rp_kernel_time * cap)()
+    n = C.c_int()
+    _check(lib().rp_get_kernel_times(scene.h, arr, cap, C.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms))
+            for i in range(min(n.value, cap))}
 
 
 # ---------------------------------------------------------------------------
