@@ -45,6 +45,23 @@ SMS, FP32_LANES = 152, 128
 # shadow ray reads a 40-byte entry
 BYTES_PER_NODE, BYTES_PER_TRI = 64, 48
 BYTES_PER_RAY = {"k_trace_closest": 32 + 28, "k_trace_shadow": 40}
+# DRAM traffic of k_trace_closest from an ncu capture of every closest-hit
+# launch of one box_blob_material_256 render at 32 spp
+# (profiles/k_trace_closest_box_blob_material_256.md): dram read + write bytes
+# per traced ray, valid while the kernel's sources hash to KERNEL_SOURCES_SHA
+TRAFFIC_CAPTURE = {"kernel": "k_trace_closest", "workload": "box_blob_material_256",
+                   "dram_bytes_per_ray": (2123.223552e6 + 440.938496e6) / 57820270.0,
+                   "sources_sha": "8f6aca8474a508c7"}
+KERNEL_SOURCES = ["rp_device.cuh", "k_wave.cu", "rp_internal.h", "rp_wave.h"]
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2406_16302_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 
@@ -322,9 +339,15 @@ def main():
     peak_tflops = SMS * FP32_LANES * 2 * peak_mhz * 1e6 / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_launch / (launch_ms / 1e3) / 1e9
+    traffic = None
+    if (dom == TRAFFIC_CAPTURE["kernel"] and args.workload == TRAFFIC_CAPTURE["workload"]
+            and kernel_sources_sha() == TRAFFIC_CAPTURE["sources_sha"]):
+        # captured at 32 spp, scaled to this launch by its rays (queue traffic
+        # grows with the rays; the BVH stays in L2)
+        traffic = TRAFFIC_CAPTURE["dram_bytes_per_ray"] * rays / launches_one_step
     achieved_tf = flops_launch / (launch_ms / 1e3) / 1e12
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": traffic,
                 "kernel": dom, "launch_ms": launch_ms,
                 "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (measured copy bandwidth)"
                               if "hbm_gbs" in peaks else "fallback 6800 GB/s",
