@@ -74,6 +74,16 @@ def lib():
         L.oracle_tangent_frame.argtypes = [P, P, P]
         L.oracle_check_mapping.argtypes = [P, C.c_int, C.c_int, C.c_uint32, C.c_uint64,
                                            C.c_uint32, C.c_uint32, P]
+        L.oracle_set_guide.argtypes = [P, P, P, C.c_int, P]
+        L.oracle_guide_encode.argtypes = [P, P, P, P]
+        L.oracle_guide_forward.argtypes = [P, P, C.c_int, P, C.c_int, P]
+        L.oracle_vmf_pdf.restype = C.c_double
+        L.oracle_vmf_pdf.argtypes = [P, C.c_double, P]
+        L.oracle_vmf_sample.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
+        L.oracle_guide_mixture.argtypes = [P, P, P, P]
+        L.oracle_mlp_forward.argtypes = [P, P, C.c_int, P]
+        L.oracle_mlp_loss_grad.restype = C.c_double
+        L.oracle_mlp_loss_grad.argtypes = [P, P, P, P, C.c_int, P]
         assert L.oracle_record_size() == RECORD_DTYPE.itemsize, "record layout mismatch"
     return _lib
 
@@ -117,6 +127,71 @@ def tangent_frame(n):
     return t, b
 
 
+# --- learned proposal (network of technique (3)'s light-side direction) ----
+
+GUIDE_IN, GUIDE_HID, GUIDE_OUT, GUIDE_LOBES = 80, 64, 48, 8
+GUIDE_LAYER_SHAPES = [(64, 80), (64, 64), (64, 64), (64, 64), (48, 64)]   # (out, in)
+GUIDE_WEIGHTS = sum(o * i for o, i in GUIDE_LAYER_SHAPES)                   # 20480
+
+
+def guide_encode(box, p, n):
+    """Integer input features of an object-space point and unit normal."""
+    b = np.ascontiguousarray(box, dtype=np.float32)
+    m = np.zeros(GUIDE_IN, dtype=np.int32)
+    lib().oracle_guide_encode(_p(b), _p(np.ascontiguousarray(p, dtype=np.float64)),
+                              _p(np.ascontiguousarray(n, dtype=np.float64)), _p(m))
+    return m
+
+
+def guide_forward(W, shift, out_exp, m):
+    """Integer network: W int32[20480], shift[4], inputs m[rows][80] -> outputs [rows][48]."""
+    W = np.ascontiguousarray(W, dtype=np.int32)
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    m = np.ascontiguousarray(np.atleast_2d(m), dtype=np.int32)
+    out = np.zeros((len(m), GUIDE_OUT))
+    lib().oracle_guide_forward(_p(W), _p(sh), int(out_exp), _p(m), len(m), _p(out))
+    return out
+
+
+def guide_mixture(o):
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    pi = np.zeros(GUIDE_LOBES); mu = np.zeros((GUIDE_LOBES, 3)); kappa = np.zeros(GUIDE_LOBES)
+    lib().oracle_guide_mixture(_p(o), _p(pi), _p(mu), _p(kappa))
+    return pi, mu, kappa
+
+
+def vmf_pdf(mu, kappa, w):
+    return lib().oracle_vmf_pdf(_p(np.ascontiguousarray(mu, dtype=np.float64)), float(kappa),
+                                _p(np.ascontiguousarray(w, dtype=np.float64)))
+
+
+def vmf_sample(mu, kappa, u1, u2):
+    w = np.zeros(3)
+    lib().oracle_vmf_sample(_p(np.ascontiguousarray(mu, dtype=np.float64)), float(kappa),
+                            float(u1), float(u2), _p(w))
+    return w
+
+
+def mlp_forward(W, x):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    out = np.zeros((len(x), GUIDE_OUT))
+    lib().oracle_mlp_forward(_p(W), _p(x), len(x), _p(out))
+    return out
+
+
+def mlp_loss_grad(W, x, omega, wt, grad=True):
+    """Mean loss -wt log q(omega) of the float network and dLoss/dW."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    wt = np.ascontiguousarray(wt, dtype=np.float64)
+    g = np.zeros(GUIDE_WEIGHTS) if grad else None
+    loss = lib().oracle_mlp_loss_grad(_p(W), _p(x), _p(om), _p(wt), len(x),
+                                      _p(g) if grad else None)
+    return (loss, g) if grad else loss
+
+
 class Oracle:
     """One scene with one edit, held by the C oracle."""
 
@@ -145,6 +220,18 @@ class Oracle:
                 for a in (edit.M1, edit.M2, edit.mat1, edit.mat2)]
         self._edit = arrs
         lib().oracle_set_edit(self.h, *[_p(a) for a in arrs])
+
+    def set_guide(self, guide):
+        """Attach an integer network (W, shift, out_exp, box) to technique (3); None detaches."""
+        if guide is None:
+            lib().oracle_set_guide(self.h, None, None, 0, None)
+            self._guide = None
+            return
+        W, shift, out_exp, box = guide
+        arrs = (np.ascontiguousarray(W, dtype=np.int32), np.ascontiguousarray(shift, dtype=np.int32),
+                np.ascontiguousarray(box, dtype=np.float32))
+        self._guide = arrs
+        lib().oracle_set_guide(self.h, _p(arrs[0]), _p(arrs[1]), int(out_exp), _p(arrs[2]))
 
     def close(self):
         if self.h:

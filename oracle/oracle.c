@@ -21,7 +21,11 @@
  *     rejected [Sec. 4.3], combined by the balance heuristic over all
  *     techniques that can produce a path [Sec. 4.3], with the path mapping
  *     operators of Sec. 5 (object transform, reconnection, random replay,
- *     rejection) and two-way mapping [Sec. 5, "Path rejection"].
+ *     rejection) and two-way mapping [Sec. 5, "Path rejection"];
+ *   - optionally, technique (3) with its first light-side direction drawn
+ *     from a learned von Mises-Fisher mixture mixed 50/50 with the cosine
+ *     density (not in the paper; an integer network evaluated exactly), and
+ *     the float network's loss and gradient used to train it.
  *
  * Readings of the paper where it is silent (each listed in the design doc):
  *   R1 area measure everywhere: |J| of object transform and of reconnection
@@ -49,7 +53,10 @@
  * the closed-form polygon irradiance; residual by exact zero for identity
  * edits, the closed-form moving-quad residual, agreement with the difference
  * of independent primal renders, mapping bijectivity and finite-difference
- * Jacobians.
+ * Jacobians.  Learned proposal: vMF density and sampler by quadrature and the
+ * closed-form cosine CDF, encoding by known angles, integer network by
+ * hand-built networks, float gradient by finite differences, guided
+ * estimator by agreement with correlated path tracing.
  */
 #include <math.h>
 #include <stdint.h>
@@ -181,6 +188,7 @@ typedef struct {
     int max_depth;
     double alpha_min, d_min, jac_max;
     double eps;
+    struct oguide_s *guide;   /* learned proposal of technique (3), or NULL */
 } oscene;
 
 static double tri_area(const tri *t) {
@@ -879,10 +887,12 @@ typedef struct {
     techmask tm;
     int residual;           /* 0: primal (plain path tracing, no MIS) */
     int64_t counters[8];
+    double vscale;          /* 0: none; else every emitted value is multiplied by it */
 } sink;
 
 static void emit(sink *k, uint32_t root, int tech, int g, int sa, int sb, int pa, vec3 va, int pb,
                  vec3 vb, int status, double Pg, double Py, double J) {
+    if (k->vscale != 0.0) { va = scale(va, k->vscale); vb = scale(vb, k->vscale); }
     if (k->img) {
         if (pa >= 0) {
             k->img[3 * pa] += va.x; k->img[3 * pa + 1] += va.y; k->img[3 * pa + 2] += va.z;
@@ -1080,6 +1090,216 @@ static void root_T2(sink *k, int g, uint32_t root, uint64_t seed) {
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* learned proposal for the light-side direction of technique (3)            */
+/*                                                                           */
+/* Not in the paper (which lists better importance sampling as future work,  */
+/* Sec. 7): a small network maps the object-space position and normal of x_D */
+/* to an 8-lobe von Mises-Fisher mixture over directions; technique (3)      */
+/* draws its first light-side direction from the defensive one-sample        */
+/* mixture q = 1/2 p_cos + 1/2 sum_j pi_j vMF_j and multiplies the values of */
+/* the root's paths by p_cos / q.  The balance-heuristic weights stay those  */
+/* of the plain techniques, so any network leaves the estimator unbiased.    */
+/*                                                                           */
+/* Inference runs on integers: inputs in [-127, 127], weights in             */
+/* [-127, 127], hidden activations in [0, 255] requantised by a right shift  */
+/* with round-half-even; every sum stays below 2^24, so any summation order  */
+/* gives the same result.                                                    */
+/* ------------------------------------------------------------------------- */
+
+enum { G_IN = 80, G_HID = 64, G_OUT = 48, G_LOBES = 8, G_LAYERS = 5 };
+static const int G_DIM_IN[G_LAYERS] = {G_IN, G_HID, G_HID, G_HID, G_HID};
+static const int G_DIM_OUT[G_LAYERS] = {G_HID, G_HID, G_HID, G_HID, G_OUT};
+static const int G_OFF[G_LAYERS + 1] = {0, 5120, 9216, 13312, 17408, 20480};
+
+typedef struct oguide_s {
+    int32_t W[20480];            /* layer l: [out][in] at G_OFF[l] */
+    int shift[4];                /* hidden requantisation right shifts */
+    int out_exp;                 /* output = z * 2^-out_exp */
+    double center[3], inv_half[3];
+} oguide;
+
+/* input features of (p, n), object space: for each coordinate c of
+ * u = clamp((p - center) * inv_half, -1, 1), then of n, the pairs
+ * sin(2^f pi c), cos(2^f pi c) for f = 0..5 (72 features), then u and n
+ * (6 features), quantised to rint(128 e) clamped to [-127, 127]; feature 78
+ * is the constant 127 and feature 79 is 0 */
+static void guide_encode(const double center[3], const double inv_half[3], vec3 p, vec3 n,
+                         int32_t m[G_IN]) {
+    double u[3] = {(p.x - center[0]) * inv_half[0], (p.y - center[1]) * inv_half[1],
+                   (p.z - center[2]) * inv_half[2]};
+    double nn[3] = {n.x, n.y, n.z};
+    double e[78];
+    int i = 0;
+    for (int c = 0; c < 3; ++c) u[c] = fmin(1.0, fmax(-1.0, u[c]));
+    for (int v = 0; v < 2; ++v)
+        for (int c = 0; c < 3; ++c)
+            for (int f = 0; f < 6; ++f) {
+                double a = ldexp(v == 0 ? u[c] : nn[c], f);
+                e[i++] = sin(PI * a);
+                e[i++] = cos(PI * a);
+            }
+    for (int c = 0; c < 3; ++c) e[i++] = u[c];
+    for (int c = 0; c < 3; ++c) e[i++] = nn[c];
+    for (int j = 0; j < 78; ++j) {
+        double q = nearbyint(128.0 * e[j]);
+        m[j] = (int32_t)fmin(127.0, fmax(-127.0, q));
+    }
+    m[78] = 127;
+    m[79] = 0;
+}
+
+/* integer forward pass: 4 hidden layers with ReLU, then the output layer */
+static void guide_forward(const oguide *gd, const int32_t m_in[G_IN], double out[G_OUT]) {
+    int64_t a[G_IN], h[G_HID];
+    for (int i = 0; i < G_IN; ++i) a[i] = m_in[i];
+    for (int l = 0; l < G_LAYERS; ++l) {
+        const int K = G_DIM_IN[l], N = G_DIM_OUT[l];
+        const int32_t *W = gd->W + G_OFF[l];
+        for (int o = 0; o < N; ++o) {
+            int64_t z = 0;
+            for (int i = 0; i < K; ++i) z += (int64_t)W[o * K + i] * a[i];
+            if (l < G_LAYERS - 1) {
+                double q = nearbyint(ldexp((double)z, -gd->shift[l]));
+                h[o] = (int64_t)fmin(255.0, fmax(0.0, q));
+            } else {
+                out[o] = ldexp((double)z, -gd->out_exp);
+            }
+        }
+        if (l < G_LAYERS - 1)
+            for (int o = 0; o < N; ++o) a[o] = h[o];
+    }
+}
+
+/* lobe j reads outputs 5j..5j+4: direction (3, normalised), log kappa
+ * (clamped to [-4, 6.2]) and the mixture logit (softmax) */
+static void guide_mixture(const double o[G_OUT], vec3 mu[G_LOBES], double kappa[G_LOBES],
+                          double pi[G_LOBES]) {
+    double mx = o[4];
+    for (int j = 1; j < G_LOBES; ++j) mx = fmax(mx, o[5 * j + 4]);
+    double sum = 0.0;
+    for (int j = 0; j < G_LOBES; ++j) { pi[j] = exp(o[5 * j + 4] - mx); sum += pi[j]; }
+    for (int j = 0; j < G_LOBES; ++j) {
+        pi[j] /= sum;
+        vec3 m = v3(o[5 * j], o[5 * j + 1], o[5 * j + 2]);
+        double l = length(m);
+        mu[j] = l > 1e-12 ? scale(m, 1.0 / l) : v3(0.0, 0.0, 1.0);
+        kappa[j] = exp(fmin(6.2, fmax(-4.0, o[5 * j + 3])));
+    }
+}
+
+/* von Mises-Fisher density on the unit sphere:
+ * kappa / (2 pi (1 - exp(-2 kappa))) exp(kappa (mu.w - 1)) */
+static double vmf_pdf(vec3 mu, double kappa, vec3 w) {
+    return kappa / (2.0 * PI * -expm1(-2.0 * kappa)) * exp(kappa * (dot(mu, w) - 1.0));
+}
+
+/* inversion sampling (Jakob 2012, "Numerically stable sampling of the von
+ * Mises Fisher distribution on S^2"): the cosine to mu is
+ * 1 + log(u1 + (1 - u1) exp(-2 kappa)) / kappa, the azimuth 2 pi u2 in the
+ * tangent frame of mu */
+static vec3 vmf_sample(vec3 mu, double kappa, double u1, double u2) {
+    double c = 1.0 + log(u1 + (1.0 - u1) * exp(-2.0 * kappa)) / kappa;
+    c = fmin(1.0, fmax(-1.0, c));
+    double s = sqrt(fmax(0.0, 1.0 - c * c)), phi = 2.0 * PI * u2;
+    vec3 t, b;
+    tangent_frame(mu, &t, &b);
+    return add(add(scale(t, s * cos(phi)), scale(b, s * sin(phi))), scale(mu, c));
+}
+
+/* linear part of a 3x4 row-major transform and of its transpose */
+static vec3 lin_M(const double *M, vec3 a) {
+    return v3(M[0] * a.x + M[1] * a.y + M[2] * a.z, M[4] * a.x + M[5] * a.y + M[6] * a.z,
+              M[8] * a.x + M[9] * a.y + M[10] * a.z);
+}
+static vec3 lin_MT(const double *M, vec3 a) {
+    return v3(M[0] * a.x + M[4] * a.y + M[8] * a.z, M[1] * a.x + M[5] * a.y + M[9] * a.z,
+              M[2] * a.x + M[6] * a.y + M[10] * a.z);
+}
+
+/* the first light-side direction of technique (3) at x_D in frame g, drawn
+ * with the numbers r of that step: u[2] < 1/2 picks the cosine component,
+ * else lobe j with (2 u[2] - 1) against the cumulative mixture weights;
+ * *ratio receives p_cos(w) / q(w) */
+static vec3 guided_direction(const oscene *s, int g, const vtx *xD, rnd4 r, double *ratio) {
+    const oguide *gd = s->guide;
+    const tri *t = &s->dyn_obj[xD->prim - s->n_static];
+    double b0 = 1.0 - xD->b1 - xD->b2;
+    vec3 p_obj = add(add(scale(t->v0, b0), scale(t->v1, xD->b1)), scale(t->v2, xD->b2));
+    vec3 nd = tri_normal(t);
+    vec3 n_obj = v3((float)nd.x, (float)nd.y, (float)nd.z);   /* the normal as stored in float */
+    int32_t m[G_IN];
+    guide_encode(gd->center, gd->inv_half, p_obj, n_obj, m);
+    double o[G_OUT];
+    guide_forward(gd, m, o);
+    vec3 mu[G_LOBES];
+    double kappa[G_LOBES], pi[G_LOBES];
+    guide_mixture(o, mu, kappa, pi);
+    vec3 w, wl;
+    if (r.u[2] < 0.5) {
+        w = cosine_dir(xD->n, r.u[0], r.u[1]);
+        wl = lin_MT(s->M[g], w);
+    } else {
+        double v = 2.0 * r.u[2] - 1.0, acc = 0.0;
+        int j = G_LOBES - 1;
+        for (int i = 0; i < G_LOBES; ++i) {
+            acc += pi[i];
+            if (v < acc) { j = i; break; }
+        }
+        wl = vmf_sample(mu[j], kappa[j], r.u[0], r.u[1]);
+        w = lin_M(s->M[g], wl);
+    }
+    double pc = cosine_pdf(xD->n, w), pv = 0.0;
+    for (int j = 0; j < G_LOBES; ++j) pv += pi[j] * vmf_pdf(mu[j], kappa[j], wl);
+    *ratio = pc / (0.5 * pc + 0.5 * pv);
+    return w;
+}
+
+/* the float network of the same shape for training: ReLU hidden layers, no
+ * biases besides the constant input feature; out[n][48] */
+static void mlp_forward_float(const double *W, const double *x, double *acts[G_LAYERS + 1]) {
+    for (int i = 0; i < G_IN; ++i) acts[0][i] = x[i];
+    for (int l = 0; l < G_LAYERS; ++l) {
+        const int K = G_DIM_IN[l], N = G_DIM_OUT[l];
+        for (int o = 0; o < N; ++o) {
+            double z = 0.0;
+            for (int i = 0; i < K; ++i) z += W[G_OFF[l] + o * K + i] * acts[l][i];
+            acts[l + 1][o] = (l < G_LAYERS - 1) ? fmax(z, 0.0) : z;
+        }
+    }
+}
+
+/* loss of one sample, -wt log sum_j pi_j vMF_j(w), and its gradient with
+ * respect to the 48 outputs (added into dout, scaled by `scale`) */
+static double mixture_nll(const double o[G_OUT], vec3 w, double wt, double scale_, double *dout) {
+    vec3 mu[G_LOBES];
+    double kappa[G_LOBES], pi[G_LOBES], v[G_LOBES], q = 0.0;
+    guide_mixture(o, mu, kappa, pi);
+    for (int j = 0; j < G_LOBES; ++j) { v[j] = vmf_pdf(mu[j], kappa[j], w); q += pi[j] * v[j]; }
+    if (dout) {
+        for (int j = 0; j < G_LOBES; ++j) {
+            double resp = pi[j] * v[j] / q;
+            double c = dot(mu[j], w);
+            dout[5 * j + 4] += scale_ * -wt * (resp - pi[j]);
+            double kr = o[5 * j + 3];
+            if (kr > -4.0 && kr < 6.2) {
+                double k = kappa[j];
+                double dlogv = 1.0 / k - 2.0 * exp(-2.0 * k) / -expm1(-2.0 * k) + (c - 1.0);
+                dout[5 * j + 3] += scale_ * -wt * resp * k * dlogv;
+            }
+            vec3 m = v3(o[5 * j], o[5 * j + 1], o[5 * j + 2]);
+            double l = length(m);
+            if (l > 1e-12) {
+                vec3 gdir = scale(sub(w, scale(mu[j], c)), kappa[j] / l);
+                dout[5 * j + 0] += scale_ * -wt * resp * gdir.x;
+                dout[5 * j + 1] += scale_ * -wt * resp * gdir.y;
+                dout[5 * j + 2] += scale_ * -wt * resp * gdir.z;
+            }
+        }
+    }
+    return -wt * log(q);
+}
+
 /* (3) dynamic two ends */
 static void root_T3(sink *k, int g, uint32_t root, uint64_t seed) {
     const oscene *s = k->s;
@@ -1094,7 +1314,12 @@ static void root_T3(sink *k, int g, uint32_t root, uint64_t seed) {
     /* light side: cosine direction about n(xD), then BSDF walk */
     {
         rnd4 r = draw(seed, root, TECH_T3, g, SIDE_LIGHT, 1);
-        vec3 w = cosine_dir(xD.n, r.u[0], r.u[1]);
+        vec3 w;
+        if (s->guide) {
+            w = guided_direction(s, g, &xD, r, &k->vscale);
+        } else {
+            w = cosine_dir(xD.n, r.u[0], r.u[1]);
+        }
         if (dot(xD.n, w) > 0.0 && trace_next(s, g, &xD, w, &yv[1]) && dot(yv[1].n, w) < 0.0 &&
             !is_black(yv[1].mat)) {
             ny = 1;
@@ -1278,6 +1503,7 @@ void oracle_destroy(void *h) {
         for (int f = 1; f <= 2; ++f) { free(s->dyn_world[f]); bvh_free(&s->dyn_bvh[f]); }
     free(s->stat); free(s->stat_mat); free(s->dyn_obj); free(s->mats);
     free(s->dyn_cdf); free(s->emit_ids); free(s->emit_cdf);
+    free(s->guide);
     free(s);
 }
 
@@ -1292,7 +1518,7 @@ static void run_roots(sink *k, int tech, int g, uint32_t r0, uint32_t r1, uint64
         switch (tech) {
         case TECH_T1: root_T1(k, g, r, seed); break;
         case TECH_T2: root_T2(k, g, r, seed); break;
-        case TECH_T3: root_T3(k, g, r, seed); break;
+        case TECH_T3: root_T3(k, g, r, seed); k->vscale = 0.0; break;
         case TECH_T7: root_PT(k, g, r, seed, TECH_T7); break;
         default: root_PT(k, g, r, seed, TECH_PT); break;
         }
@@ -1501,4 +1727,100 @@ int oracle_check_mapping(void *h, int tech, int g, uint32_t spp, uint64_t seed, 
     out[2] = mc.max_pos_err; out[3] = mc.max_jac_err;
     out[4] = (double)mc.n_jac_checked; out[5] = mc.max_fd_err;
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* learned proposal: entry points                                            */
+/* ------------------------------------------------------------------------- */
+
+/* attach an integer network to technique (3) of this scene (W = NULL
+ * detaches): W[20480] layer-major [out][in], shift[4], out_exp, box =
+ * (center xyz, inverse half extent xyz) of the object-space inputs */
+int oracle_set_guide(void *h, const int32_t *W, const int32_t *shift, int out_exp,
+                     const float *box) {
+    oscene *s = (oscene *)h;
+    free(s->guide);
+    s->guide = NULL;
+    if (!W) return 0;
+    oguide *gd = (oguide *)calloc(1, sizeof(oguide));
+    memcpy(gd->W, W, sizeof gd->W);
+    for (int l = 0; l < 4; ++l) gd->shift[l] = shift[l];
+    gd->out_exp = out_exp;
+    for (int c = 0; c < 3; ++c) { gd->center[c] = box[c]; gd->inv_half[c] = box[3 + c]; }
+    s->guide = gd;
+    return 0;
+}
+
+void oracle_guide_encode(const float *box, const double *p, const double *n, int32_t *m) {
+    double c[3] = {box[0], box[1], box[2]}, ih[3] = {box[3], box[4], box[5]};
+    guide_encode(c, ih, v3(p[0], p[1], p[2]), v3(n[0], n[1], n[2]), m);
+}
+
+/* rows of integer inputs m[rows][80] -> out[rows][48] */
+void oracle_guide_forward(const int32_t *W, const int32_t *shift, int out_exp, const int32_t *m,
+                          int rows, double *out) {
+    oguide *gd = (oguide *)calloc(1, sizeof(oguide));
+    memcpy(gd->W, W, sizeof gd->W);
+    for (int l = 0; l < 4; ++l) gd->shift[l] = shift[l];
+    gd->out_exp = out_exp;
+    for (int r = 0; r < rows; ++r) guide_forward(gd, m + (size_t)r * G_IN, out + (size_t)r * G_OUT);
+    free(gd);
+}
+
+double oracle_vmf_pdf(const double *mu, double kappa, const double *w) {
+    return vmf_pdf(v3(mu[0], mu[1], mu[2]), kappa, v3(w[0], w[1], w[2]));
+}
+
+void oracle_vmf_sample(const double *mu, double kappa, double u1, double u2, double *w) {
+    vec3 r = vmf_sample(v3(mu[0], mu[1], mu[2]), kappa, u1, u2);
+    w[0] = r.x; w[1] = r.y; w[2] = r.z;
+}
+
+/* mixture of network outputs o[48]: pi[8], mu[8][3], kappa[8] */
+void oracle_guide_mixture(const double *o, double *pi, double *mu, double *kappa) {
+    vec3 m[G_LOBES];
+    guide_mixture(o, m, kappa, pi);
+    for (int j = 0; j < G_LOBES; ++j) { mu[3 * j] = m[j].x; mu[3 * j + 1] = m[j].y; mu[3 * j + 2] = m[j].z; }
+}
+
+/* float network: out[rows][48] for inputs x[rows][80] */
+void oracle_mlp_forward(const double *W, const double *x, int rows, double *out) {
+    double a0[G_IN], a1[G_HID], a2[G_HID], a3[G_HID], a4[G_HID], a5[G_OUT];
+    double *acts[G_LAYERS + 1] = {a0, a1, a2, a3, a4, a5};
+    for (int r = 0; r < rows; ++r) {
+        mlp_forward_float(W, x + (size_t)r * G_IN, acts);
+        memcpy(out + (size_t)r * G_OUT, a5, sizeof a5);
+    }
+}
+
+/* mean loss (1/rows) sum_r -wt_r log q(w_r) of the float network and its
+ * gradient grad[20480] with respect to W (back-propagation through the
+ * mixture, the output layer and the ReLU layers) */
+double oracle_mlp_loss_grad(const double *W, const double *x, const double *omega,
+                            const double *wt, int rows, double *grad) {
+    double a0[G_IN], a1[G_HID], a2[G_HID], a3[G_HID], a4[G_HID], a5[G_OUT];
+    double *acts[G_LAYERS + 1] = {a0, a1, a2, a3, a4, a5};
+    double loss = 0.0;
+    if (grad) memset(grad, 0, sizeof(double) * 20480);
+    for (int r = 0; r < rows; ++r) {
+        mlp_forward_float(W, x + (size_t)r * G_IN, acts);
+        double dcur[G_HID] = {0}, dprev[G_IN];
+        const double *om = omega + 3 * (size_t)r;
+        loss += mixture_nll(a5, v3(om[0], om[1], om[2]), wt[r], 1.0 / rows, grad ? dcur : NULL) / rows;
+        if (!grad) continue;
+        for (int l = G_LAYERS - 1; l >= 0; --l) {
+            const int K = G_DIM_IN[l], N = G_DIM_OUT[l];
+            /* dcur: gradient of the layer's pre-activation output z_l */
+            for (int o = 0; o < N; ++o)
+                for (int i = 0; i < K; ++i) grad[G_OFF[l] + o * K + i] += dcur[o] * acts[l][i];
+            if (l == 0) break;
+            for (int i = 0; i < K; ++i) {
+                double d = 0.0;
+                for (int o = 0; o < N; ++o) d += W[G_OFF[l] + o * K + i] * dcur[o];
+                dprev[i] = acts[l][i] > 0.0 ? d : 0.0;     /* ReLU of the layer below */
+            }
+            for (int i = 0; i < K; ++i) dcur[i] = dprev[i];
+        }
+    }
+    return loss;
 }

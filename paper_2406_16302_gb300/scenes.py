@@ -519,3 +519,43 @@ def light_quads(scene: Scene):
     """Emissive triangles of a scene, as (tri index, material row) pairs."""
     em = scene.materials[:, 8:11].sum(axis=1) > 0
     return np.nonzero(em[scene.static_material])[0]
+
+
+# --- seeded networks for the learned proposal of technique (3) --------------
+
+GUIDE_LAYER_SHAPES = [(64, 80), (64, 64), (64, 64), (64, 64), (48, 64)]   # (out, in)
+
+
+def guide_box(vertices):
+    """(center xyz, inverse half extent xyz) of an object-space vertex array:
+    the normalisation of the proposal network's position input."""
+    v = np.asarray(vertices, dtype=np.float64)
+    lo, hi = v.min(axis=0), v.max(axis=0)
+    c = 0.5 * (lo + hi)
+    h = np.maximum(0.5 * (hi - lo), 1e-6)
+    return np.concatenate([c, 1.0 / h]).astype(np.float32)
+
+
+def random_int_guide(seed, box, shifts=(9, 9, 9, 10), out_exp=12):
+    """A seeded integer network: weights uniform in [-127, 127], the given
+    hidden requantisation shifts and output exponent."""
+    rng = np.random.default_rng(seed)
+    W = rng.integers(-127, 128, size=sum(o * i for o, i in GUIDE_LAYER_SHAPES)).astype(np.int32)
+    return W, np.asarray(shifts, dtype=np.int32), int(out_exp), np.asarray(box, dtype=np.float32)
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest bfloat16 (ties to even), as float32."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    a = (a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000
+    return a.astype(np.uint32).view(np.float32)
+
+
+def random_float_guide(seed, gain=1.0):
+    """Seeded float weights of the same network (He initialisation, rounded
+    to bfloat16 so that both precisions start from the same values)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for o, i in GUIDE_LAYER_SHAPES:
+        out.append(rng.normal(0.0, gain * np.sqrt(2.0 / i), size=o * i))
+    return bf16_round(np.concatenate(out).astype(np.float32)).astype(np.float64)

@@ -125,11 +125,14 @@ def _job(args):
         sys.path.insert(0, ROOT)
     import oracle
     from paper_2406_16302_gb300 import scenes
-    kind, builder, bargs, seed, spp, mask, edit_kind = args
+    kind, builder, bargs, seed, spp, mask, edit_kind, guide = args
     scene, edit = getattr(scenes, builder)(**bargs)
     if edit_kind == "identity":
         edit = scenes.identity_edit(edit)
     o = oracle.Oracle(scene, edit)
+    if guide is not None:
+        gseed, gkw = guide
+        o.set_guide(scenes.random_int_guide(gseed, scenes.guide_box(scene.dyn_vertices), **gkw))
     if kind == "corr":
         return o.render_primal(2, spp, seed) - o.render_primal(1, spp, seed)
     if kind == "p1":
@@ -139,8 +142,10 @@ def _job(args):
     return o.render_residual(spp, seed, tech_mask=mask)
 
 
-def run_many(kind, builder, bargs, seeds, spp, mask=15, edit_kind=None, procs=None):
-    jobs = [(kind, builder, bargs, s, spp, mask, edit_kind) for s in seeds]
+def run_many(kind, builder, bargs, seeds, spp, mask=15, edit_kind=None, procs=None, guide=None):
+    """Independent oracle renders, one per seed.  guide = (seed, kwargs) of
+    a seeded integer proposal network for technique (3)."""
+    jobs = [(kind, builder, bargs, s, spp, mask, edit_kind, guide) for s in seeds]
     procs = procs or min(len(jobs), os.cpu_count() or 1)
     if procs <= 1:
         return np.array([_job(j) for j in jobs])
