@@ -230,6 +230,88 @@ typedef struct {
 rp_status rp_enable_timing(rp_scene *scene, int on);
 rp_status rp_get_kernel_times(rp_scene *scene, rp_kernel_time *out, int capacity, int *count);
 
+/* ------------------------------------------------------------------------
+ * Learned proposal for technique (3) (not in the paper, which names better
+ * importance sampling as future work in Sec. 7).  A small network maps the
+ * object-space position and normal of x_D to an 8-lobe von Mises-Fisher
+ * mixture over directions.  With a guide attached to a scene, technique (3)
+ * draws its first light-side direction from the defensive one-sample
+ * mixture q = p_cos / 2 + (vMF mixture) / 2 and multiplies the values of the
+ * root's paths by p_cos / q; the balance-heuristic weights of Sec. 4.3 stay
+ * those of the plain techniques, so every network leaves the residual
+ * estimator unbiased.
+ *
+ * Network: 80 input features, four hidden layers of 64 with ReLU, 48
+ * outputs (lobe j: direction 5j..5j+2, log kappa 5j+3 clamped to
+ * [-4, 6.2], logit 5j+4; 40..47 unused); weights layer-major [out][in]:
+ * 64x80, 64x64, 64x64, 64x64, 48x64 (20480 values), no biases besides the
+ * constant input feature.  Features of (p, n): for each coordinate of
+ * u = clamp((p - center) * inv_half, -1, 1), then of n, sin(2^f pi c) and
+ * cos(2^f pi c) for f = 0..5; then u; then n; then a constant and a zero.
+ *
+ * Rendering uses an integer network: inputs rint(128 e) in [-127, 127]
+ * (the constant is 127), weights in [-127, 127], hidden activations
+ * clamp(rint(z 2^-shift_l), 0, 255) (round half to even), outputs
+ * z 2^-out_exp.  Every partial sum stays below 2^24, so the BF16 tensor-core
+ * products with FP32 accumulation are exact.  Training uses the float
+ * network (BF16 operands, FP32 accumulation) and the weighted loss
+ * -sum_i wt_i log q_vmf(w_i) / sum_i wt_i over samples of guided renders
+ * (w_i the drawn direction in object space, wt_i the magnitude of what
+ * the root added to the image); each step ends with Adam and a
+ * re-quantisation into the integer network. */
+typedef struct rp_guide_s rp_guide;
+
+/* box: (center xyz, inverse half extent xyz) of object-space positions;
+ * batch: training samples per step (even, in [256, 2^24]; half per frame,
+ * the roots below batch / 2 of each frame's technique (3)); seed: He
+ * initialisation of the float network.  The guide has no integer network
+ * until rp_guide_set_int or the first rp_guide_train_step: until then
+ * technique (3) samples as without a guide and only collects samples.
+ * Synchronous.  Errors: RP_ERR_INVALID_ARG, RP_ERR_OOM, RP_ERR_CUDA. */
+rp_status rp_guide_create(const float *box, uint32_t batch, uint64_t seed, rp_guide **out);
+void rp_guide_destroy(rp_guide *guide);
+
+/* Float network weights (host arrays of 20480 floats); setting resets Adam. */
+rp_status rp_guide_set_weights(rp_guide *guide, const float *weights);
+rp_status rp_guide_get_weights(rp_guide *guide, float *weights);
+
+/* Integer network used by renders: weights[20480] in [-127, 127], shift[4]
+ * in [0, 24], out_exp in [-30, 60].  Synchronous. */
+rp_status rp_guide_set_int(rp_guide *guide, const int8_t *weights, const int32_t *shift,
+                           int32_t out_exp);
+rp_status rp_guide_get_int(rp_guide *guide, int8_t *weights, int32_t *shift, int32_t *out_exp);
+
+/* Integer network on n rows of device features d_in[n][80] (int8) into
+ * d_out[n][48] (float, exact).  Asynchronous; a tensor-core wait that
+ * times out is reported by rp_guide_status. */
+rp_status rp_guide_infer(rp_guide *guide, const int8_t *d_in, uint32_t n, float *d_out,
+                         void *stream);
+
+/* Float network: the mean loss (1/n) sum_i -wt_i log q_vmf(w_i) of n rows
+ * (d_x[n][80] features, rounded to BF16; d_omega[n][3] unit directions;
+ * d_wt[n] weights; rows with wt <= 0 add nothing) and its gradient with
+ * respect to the weights, ADDED into d_grad[20480] and d_loss[1].
+ * Asynchronous. */
+rp_status rp_guide_loss_grad(rp_guide *guide, const float *d_x, const float *d_omega,
+                             const float *d_wt, uint32_t n, float *d_grad, float *d_loss,
+                             void *stream);
+
+/* One training step on the samples of the most recent guided render: batch
+ * features, loss gradient, Adam (lr; beta 0.9, 0.99), re-quantisation.
+ * Synchronises `stream`; *loss receives the weighted loss (may be NULL).
+ * Errors: RP_ERR_TIMEOUT (a tensor-core wait gave up), RP_ERR_CUDA. */
+rp_status rp_guide_train_step(rp_guide *guide, float lr, float *loss, void *stream);
+
+/* RP_ERR_TIMEOUT if a guide kernel's tensor-core wait gave up (synchronises
+ * the device). */
+rp_status rp_guide_status(rp_guide *guide);
+
+/* Attach a guide to a scene's technique (3) for the renders that follow
+ * (NULL detaches).  The guide must outlive its attachment.  The
+ * one-thread-per-root entry point (rp_render_residual_f32_noalloc) never
+ * uses it. */
+rp_status rp_scene_set_guide(rp_scene *scene, rp_guide *guide);
+
 /* Thread-local message describing the last error (empty string if none). */
 const char *rp_last_error(void);
 

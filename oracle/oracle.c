@@ -1270,17 +1270,33 @@ static void mlp_forward_float(const double *W, const double *x, double *acts[G_L
 }
 
 /* loss of one sample, -wt log sum_j pi_j vMF_j(w), and its gradient with
- * respect to the 48 outputs (added into dout, scaled by `scale`) */
+ * respect to the 48 outputs (added into dout, scaled by `scale_`); the sum
+ * is taken in log space, log pi_j + log vMF_j(w), so that no lobe
+ * underflows */
 static double mixture_nll(const double o[G_OUT], vec3 w, double wt, double scale_, double *dout) {
     vec3 mu[G_LOBES];
-    double kappa[G_LOBES], pi[G_LOBES], v[G_LOBES], q = 0.0;
+    double kappa[G_LOBES], pi[G_LOBES], lv[G_LOBES], lpi[G_LOBES];
     guide_mixture(o, mu, kappa, pi);
-    for (int j = 0; j < G_LOBES; ++j) { v[j] = vmf_pdf(mu[j], kappa[j], w); q += pi[j] * v[j]; }
+    double lmax = o[4];
+    for (int j = 1; j < G_LOBES; ++j) lmax = fmax(lmax, o[5 * j + 4]);
+    double ls = 0.0;
+    for (int j = 0; j < G_LOBES; ++j) ls += exp(o[5 * j + 4] - lmax);
+    double lse = lmax + log(ls);
+    double mx = -INFINITY;
+    for (int j = 0; j < G_LOBES; ++j) {
+        double k = kappa[j];
+        lpi[j] = o[5 * j + 4] - lse;
+        lv[j] = lpi[j] + log(k) - log(2.0 * PI) - log(-expm1(-2.0 * k)) + k * (dot(mu[j], w) - 1.0);
+        mx = fmax(mx, lv[j]);
+    }
+    double s = 0.0;
+    for (int j = 0; j < G_LOBES; ++j) s += exp(lv[j] - mx);
+    double logq = mx + log(s);
     if (dout) {
         for (int j = 0; j < G_LOBES; ++j) {
-            double resp = pi[j] * v[j] / q;
+            double resp = exp(lv[j] - logq);
             double c = dot(mu[j], w);
-            dout[5 * j + 4] += scale_ * -wt * (resp - pi[j]);
+            dout[5 * j + 4] += scale_ * -wt * (resp - exp(lpi[j]));
             double kr = o[5 * j + 3];
             if (kr > -4.0 && kr < 6.2) {
                 double k = kappa[j];
@@ -1297,7 +1313,7 @@ static double mixture_nll(const double o[G_OUT], vec3 w, double wt, double scale
             }
         }
     }
-    return -wt * log(q);
+    return -wt * logq;
 }
 
 /* (3) dynamic two ends */

@@ -95,7 +95,8 @@ __device__ __forceinline__ void emit_nomotion(Ctx &cx, PathCounts &pc, uint32_t 
         ++pc.accepted;
         const float den = (Pg + Py) / invN;
         const float3 va = fx * (sign / den), vb = fy * (-sign / den);
-        if (A.rec_count) {
+        if (A.rec_count || (tech == T_3 && A.G.on)) {
+            // records, or the learned proposal's value ratio and sample weights
             emit(cx, root, tech, A.frame, sa, sb, pa, va, pa, vb, MAP_ACCEPT, Pg, Py, 1.0f);
         } else if (A.img) {
             splat(A.img, pa, va + vb);    // both splats land on one pixel

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 
 #include "chain_fast.cuh"
+#include "guide_device.cuh"
 #include "rp_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -136,9 +137,45 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                 if (!vtx_black(c, g, xD) && in_image_facing(c, xD))
                     push_shadow(A, 0, xD, camera_vertex(c), make_tag(r, CK_CAMERA, 0));
             } else {
-                if (D >= 4 && !vtx_black(c, g, xD)) {
+                const bool live = D >= 4 && !vtx_black(c, g, xD);
+                if (A.G.on) {
+                    // learned proposal: object-space x_D and normal for the
+                    // network's input and the training samples
+                    const float4 ur = draw(A.seed, root, T_3, g, SD_ROOT, 0);
+                    const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
+                    double b1, b2;
+                    tri_sample(ur.y, ur.z, b1, b2);
+                    const float4 ta = A.S.dyn_tri[3 * q], tb = A.S.dyn_tri[3 * q + 1],
+                                 tcv = A.S.dyn_tri[3 * q + 2];
+                    const double3 v0 = d3(ta);
+                    const double3 po = dadd(dadd(v0, dscale(dsub(d3(tb), v0), b1)),
+                                            dscale(dsub(d3(tcv), v0), b2));
+                    const float3 no = f3(ta.w, tb.w, tcv.w);
+                    const uint32_t slot = guide_slot(A.G, g, root);
+                    if (slot != ~0u) {
+                        const uint32_t C = A.G.smp.cap;
+                        A.G.smp.p[slot] = (float)po.x; A.G.smp.p[C + slot] = (float)po.y;
+                        A.G.smp.p[2 * C + slot] = (float)po.z;
+                        A.G.smp.n[slot] = no.x; A.G.smp.n[C + slot] = no.y; A.G.smp.n[2 * C + slot] = no.z;
+                        A.G.smp.wt[slot] = 0.f;
+                    }
+                    if (A.G.use_net) {
+                        if (live) W.flags[r] = RF_GUIDE;
+                        continue;       // encoded by k_encode3, drawn after inference by k_start3g
+                    }
+                }
+                if (live) {
                     float4 u = draw(A.seed, root, T_3, g, SD_LIGHT, 1);
                     float3 w = cosine_dir_walk(A.S, xD.n, u.x, u.y);
+                    if (A.G.on) {
+                        const uint32_t slot = guide_slot(A.G, g, root);
+                        if (slot != ~0u) {
+                            const double3 wl = dlinear_T(A.E.M[g], d3(w));
+                            const uint32_t C = A.G.smp.cap;
+                            A.G.smp.w[slot] = (float)wl.x; A.G.smp.w[C + slot] = (float)wl.y;
+                            A.G.smp.w[2 * C + slot] = (float)wl.z;
+                        }
+                    }
                     if (dot3(xD.n, w) > 0.f) push_closest(A, 0, 0, xD.p, w, xD.prim, make_tag(r, SIDE_LIGHT, 1));
                 }
             }
@@ -152,6 +189,73 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
             float3 d = camera_dir(A.S, pix % A.S.W, pix / A.S.W, u.x, u.y);
             push_closest(A, 0, 0, A.S.cam_pos, d, -1, make_tag(r, SIDE_ROOT, 0));
         }
+    }
+}
+
+// technique (3) with the learned proposal: the network's integer input
+// features of x_D (object space, recomputed from the root's numbers)
+__global__ void __launch_bounds__(128) k_encode3(const __grid_constant__ LaunchArgs A) {
+    const uint32_t n = A.root_end - A.root_begin;
+    const int g = A.frame;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        if (!(A.W.flags[r] & RF_GUIDE)) continue;
+        const uint32_t root = A.root_begin + r;
+        const float4 ur = draw(A.seed, root, T_3, g, SD_ROOT, 0);
+        const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
+        double b1, b2;
+        tri_sample(ur.y, ur.z, b1, b2);
+        const float4 ta = A.S.dyn_tri[3 * q], tb = A.S.dyn_tri[3 * q + 1], tcv = A.S.dyn_tri[3 * q + 2];
+        const double3 v0 = d3(ta);
+        const double3 po = dadd(dadd(v0, dscale(dsub(d3(tb), v0), b1)), dscale(dsub(d3(tcv), v0), b2));
+        guide_encode_d(A.G.net.box, po, f3(ta.w, tb.w, tcv.w), A.G.gin + (size_t)r * kGIn);
+    }
+}
+
+// technique (3) with the learned proposal: draw the first light-side
+// direction from q = p_cos / 2 + (vMF mixture of the network's outputs) / 2
+// with the step's numbers (u.z < 1/2 picks the cosine part, else 2 u.z - 1
+// picks a lobe), record p_cos / q for the root's values
+__global__ void __launch_bounds__(256) k_start3g(const __grid_constant__ LaunchArgs A) {
+    const uint32_t n = A.root_end - A.root_begin;
+    const WaveBuf &W = A.W;
+    Ctx c(A, nullptr);
+    const int g = A.frame;
+    const float *M = A.E.M[g];
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        if (!(W.flags[r] & RF_GUIDE)) continue;
+        const uint32_t root = A.root_begin + r;
+        const Vtx xD = load_vtx(c, W, 0, r);
+        const float4 u = draw(A.seed, root, T_3, g, SD_LIGHT, 1);
+        MixD mix;
+        guide_mixture_d(A.G.gout + (size_t)r * kGOut, mix);
+        const double3 nw = d3(xD.n);
+        double3 w, wl;
+        if (u.z < 0.5f) {
+            w = cosine_dir_d(A.S, nw, u.x, u.y);
+            wl = dlinear_T(M, w);
+        } else {
+            const double v = 2.0 * (double)u.z - 1.0;
+            double acc = 0.0;
+            int j = kGLobes - 1;
+            for (int i = 0; i < kGLobes; ++i) {
+                acc += mix.pi[i];
+                if (v < acc) { j = i; break; }
+            }
+            wl = vmf_sample_d(A.S, mix.mu[j], mix.kappa[j], u.x, u.y);
+            w = dlinear(M, wl);
+        }
+        const double cw = ddot(nw, w);
+        const double pc = cw > 0.0 ? cw / kPiD : 0.0;
+        const double pv = mix_pdf_d(mix, wl);
+        A.G.gratio[r] = (float)(pc / (0.5 * pc + 0.5 * pv));
+        const uint32_t slot = guide_slot(A.G, g, root);
+        if (slot != ~0u) {
+            const uint32_t C = A.G.smp.cap;
+            A.G.smp.w[slot] = (float)wl.x; A.G.smp.w[C + slot] = (float)wl.y;
+            A.G.smp.w[2 * C + slot] = (float)wl.z;
+        }
+        const float3 wf = tof(w);
+        if (dot3(xD.n, wf) > 0.f) push_closest(A, 0, 0, xD.p, wf, xD.prim, make_tag(r, SIDE_LIGHT, 1));
     }
 }
 
@@ -561,6 +665,15 @@ cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.W.counts, 0, sizeof(unsigned int) * kCountSlots, s);
     if (e != cudaSuccess) return e;
     RP_LAUNCH("k_gen", gR, 256, k_gen<T>, a);
+    if (T == T_3 && a.G.use_net) {
+        RP_LAUNCH("k_encode3", gR, 128, k_encode3, a);
+        cudaEvent_t e0_ = nullptr, e1_ = nullptr;
+        if (a.timer) timer_begin(a.timer, s, &e0_, &e1_);
+        e = launch_guide_infer(a.G.net, a.G.gin, n, a.G.gout, a.G.err, s);
+        if (a.timer) timer_end(a.timer, "k_guide_infer", s, e0_, e1_);
+        if (e != cudaSuccess) return e;
+        RP_LAUNCH("k_start3g", gR, 256, k_start3g, a);
+    }
     int it0 = 1;
     if (T == T_1 || T == T_2) {
         RP_LAUNCH("k_trace_shadow", gQ, kBlock, k_trace_shadow, a, 0);

@@ -56,6 +56,34 @@ rp_status upload(const std::vector<T> &h, T **d) {
 
 }  // namespace
 
+struct rp_guide_s {
+    float box[6] = {0, 0, 0, 1, 1, 1};
+    uint32_t cap = 0;                  // training samples per step (both frames)
+    std::vector<void *> allocs;
+    // float network, Adam state, gradient, loss, activation maxima
+    float *Wm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
+    float *wsum = nullptr, *d_box = nullptr;
+    unsigned int *amax = nullptr;
+    int *err = nullptr;
+    __nv_bfloat16 *Wbf = nullptr, *Wq = nullptr;
+    // samples gathered by guided renders and the training batch built from them
+    GuideSamples smp{};
+    __nv_bfloat16 *X = nullptr;
+    float *omega = nullptr, *wt = nullptr;
+    // scratch of rp_guide_loss_grad
+    __nv_bfloat16 *Xs = nullptr;
+    size_t xs_rows = 0;
+    // integer network used by renders
+    bool has_int = false;
+    int shift[4] = {0, 0, 0, 0};
+    int out_exp = 0;
+    int adam_t = 0;
+    ~rp_guide_s() {
+        for (void *p : allocs) cudaFree(p);
+        if (Xs) cudaFree(Xs);
+    }
+};
+
 struct rp_scene_s {
     DevScene S{};
     std::vector<void *> allocs;
@@ -71,11 +99,24 @@ struct rp_scene_s {
     uint32_t wave_cap = 1u << 22;  // roots per wave
     KernelTimer timer;
     bool timing_on = false;
+    // learned proposal of technique (3) and its per-root buffers
+    rp_guide *guide = nullptr;
+    int8_t *gin = nullptr;
+    float *gout = nullptr, *gratio = nullptr;
+    uint32_t guide_R = 0;
+    void free_guide_buffers() {
+        if (gin) cudaFree(gin);
+        if (gout) cudaFree(gout);
+        if (gratio) cudaFree(gratio);
+        gin = nullptr; gout = nullptr; gratio = nullptr;
+        guide_R = 0;
+    }
     void free_wave() {
         for (void *p : wave_allocs) cudaFree(p);
         wave_allocs.clear();
         W = WaveBuf{};
         wave_tasks = false;
+        free_guide_buffers();
     }
     ~rp_scene_s() {
         for (void *p : allocs) cudaFree(p);
@@ -367,6 +408,20 @@ static LaunchArgs base_args(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64
     a.stats = sc->stats_on ? sc->d_stats : nullptr;
     a.residual = 1;
     a.timer = sc->timing_on ? &sc->timer : nullptr;
+    if (rp_guide *gd = sc->guide) {
+        a.G.on = 1;
+        a.G.use_net = gd->has_int ? 1 : 0;
+        a.G.net.Wq = gd->Wq;
+        for (int l = 0; l < 4; ++l) a.G.net.hid_scale[l] = std::ldexp(1.0f, -gd->shift[l]);
+        a.G.net.out_scale = std::ldexp(1.0f, -gd->out_exp);
+        for (int i = 0; i < 6; ++i) a.G.net.box[i] = gd->box[i];
+        a.G.smp = gd->smp;
+        a.G.half = gd->cap / 2;
+        a.G.err = gd->err;
+        a.G.gin = sc->gin;
+        a.G.gout = sc->gout;
+        a.G.gratio = sc->gratio;
+    }
     return a;
 }
 
@@ -381,9 +436,25 @@ static rp_status check_render(rp_scene *sc, uint32_t spp, uint32_t mask) {
 
 // wavefront buffers for waves of up to R roots; `tasks` adds the mapping
 // task queue needed by edits with motion
+static rp_status ensure_guide_buffers(rp_scene *sc) {
+    if (!sc->guide || sc->guide_R >= sc->W.R) return RP_OK;
+    sc->free_guide_buffers();
+    const size_t R = sc->W.R;
+    cudaError_t e = cudaMalloc((void **)&sc->gin, R * kGIn);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sc->gout, R * kGOut * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sc->gratio, R * sizeof(float));
+    if (e != cudaSuccess) {
+        sc->free_guide_buffers();
+        return e == cudaErrorMemoryAllocation ? fail(RP_ERR_OOM, "guide buffer allocation failed")
+                                              : cuda_fail(e, "cudaMalloc guide buffers");
+    }
+    sc->guide_R = sc->W.R;
+    return RP_OK;
+}
+
 static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
     const int D = sc->S.max_depth;
-    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return RP_OK;
+    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return ensure_guide_buffers(sc);
     R = std::max(R, sc->W.R);
     tasks = tasks || sc->wave_tasks;
     sc->free_wave();
@@ -421,7 +492,7 @@ static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
     A_(W.counts, kCountSlots * 4ull)
 #undef A_
     sc->wave_tasks = tasks;
-    return RP_OK;
+    return ensure_guide_buffers(sc);
 }
 
 // run roots [r0, r1) of technique `tech` (0: primal) in frame a.frame as waves
@@ -432,6 +503,9 @@ static rp_status run_waves(rp_scene *sc, LaunchArgs a, int tech, uint32_t r0, ui
     if (n == 0) return RP_OK;
     if (rp_status s = ensure_wave(sc, std::min(n, sc->wave_cap), tasks)) return s;
     a.W = sc->W;
+    a.G.gin = sc->gin;
+    a.G.gout = sc->gout;
+    a.G.gratio = sc->gratio;
     for (uint32_t b = r0; b < r1; b += sc->W.R) {
         a.root_begin = b;
         a.root_end = std::min(r1, b + sc->W.R);
@@ -448,6 +522,9 @@ static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint6
     const uint32_t N = spp * (uint32_t)(sc->S.W * sc->S.H);
     if (sc->stats_on)
         RP_CUDA(cudaMemsetAsync(sc->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, st), "memset");
+    if (sc->guide && (mask & RP_TECH_DYNAMIC_TWO_ENDS))
+        RP_CUDA(cudaMemsetAsync(sc->guide->smp.wt, 0, sizeof(float) * sc->guide->cap, st),
+                "memset guide weights");
     const int techs[4] = {1, 2, 3, 7};
     for (int g = 1; g <= 2; ++g)
         for (int t = 0; t < 4; ++t) {
@@ -464,6 +541,7 @@ static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint6
 static rp_status render_into_direct(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
                                     uint32_t mask, double *d_out, cudaStream_t st) {
     LaunchArgs a = base_args(sc, E, spp, seed, mask);
+    a.G = GuideLaunch{};           // the one-thread-per-root kernels run without the proposal
     a.img = d_out;
     a.root_begin = 0;
     a.root_end = spp * (uint32_t)(sc->S.W * sc->S.H);
@@ -678,3 +756,278 @@ rp_status render_residual_into(rp_scene *scene, const rp_edit_handle *edit, uint
 }
 
 }  // namespace rp
+
+// ---------------------------------------------------------------------------
+// learned proposal of technique (3)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// splitmix64 and Box-Muller: the seeded He initialisation of the float network
+uint64_t splitmix(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double unit_open(uint64_t &s) { return ((double)(splitmix(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+rp_status guide_alloc(rp_guide *g, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) return fail(RP_ERR_OOM, "guide allocation failed");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc guide");
+    g->allocs.push_back(*p);
+    return cudaMemset(*p, 0, bytes) == cudaSuccess ? RP_OK : fail(RP_ERR_CUDA, "memset guide");
+}
+
+rp_status upload_float_weights(rp_guide *g, const float *h) {
+    RP_CUDA(cudaMemcpy(g->Wm, h, sizeof(float) * kGWeights, cudaMemcpyHostToDevice), "upload weights");
+    RP_CUDA(cudaMemset(g->m, 0, sizeof(float) * kGWeights), "reset adam");
+    RP_CUDA(cudaMemset(g->v, 0, sizeof(float) * kGWeights), "reset adam");
+    RP_CUDA(launch_f32_to_bf16(g->Wm, g->Wbf, kGWeights, 0), "convert weights");
+    RP_CUDA(cudaDeviceSynchronize(), "convert weights");
+    g->adam_t = 0;
+    return RP_OK;
+}
+
+rp_status upload_int_network(rp_guide *g, const int8_t *W, const int32_t *shift, int32_t out_exp) {
+    for (int l = 0; l < 4; ++l)
+        if (shift[l] < 0 || shift[l] > 24) return fail(RP_ERR_INVALID_ARG, "shift must be in [0, 24]");
+    if (out_exp < -30 || out_exp > 60) return fail(RP_ERR_INVALID_ARG, "out_exp must be in [-30, 60]");
+    std::vector<float> f(kGWeights);
+    for (int i = 0; i < kGWeights; ++i) {
+        if (W[i] < -127) return fail(RP_ERR_INVALID_ARG, "integer weights must be in [-127, 127]");
+        f[i] = (float)W[i];
+    }
+    float *tmp = nullptr;
+    RP_CUDA(cudaMalloc((void **)&tmp, sizeof(float) * kGWeights), "cudaMalloc");
+    cudaError_t e = cudaMemcpy(tmp, f.data(), sizeof(float) * kGWeights, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_f32_to_bf16(tmp, g->Wq, kGWeights, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "upload integer network");
+    for (int l = 0; l < 4; ++l) g->shift[l] = shift[l];
+    g->out_exp = out_exp;
+    g->has_int = true;
+    return RP_OK;
+}
+
+// integer network from the float one: per layer the largest power-of-two
+// weight scale with |W| 2^s <= 127, activation scales 2^t with the largest
+// recorded activation <= 255 (2^7 for the inputs), requantisation shifts
+// t_l + s_l - t_{l+1} (never negative)
+rp_status quantize(rp_guide *g, const float *W, const float *amax) {
+    std::vector<int8_t> q(kGWeights);
+    int s[kGLayers], t[kGLayers];
+    t[0] = 7;
+    for (int l = 0; l < kGLayers; ++l) {
+        float mx = 0.f;
+        for (int i = guide_off(l); i < guide_off(l + 1); ++i) mx = std::max(mx, std::fabs(W[i]));
+        s[l] = mx > 0.f ? (int)std::floor(std::log2(127.0 / mx)) : 0;
+        s[l] = std::max(-20, std::min(30, s[l]));
+        for (int i = guide_off(l); i < guide_off(l + 1); ++i) {
+            double v = std::nearbyint(std::ldexp((double)W[i], s[l]));
+            q[i] = (int8_t)std::max(-127.0, std::min(127.0, v));
+        }
+    }
+    int32_t shift[4];
+    for (int l = 0; l < 4; ++l) {
+        int tn = amax[l] > 0.f ? (int)std::floor(std::log2(255.0 / amax[l])) : t[l] + s[l];
+        int sh = t[l] + s[l] - tn;
+        if (sh < 0) { sh = 0; tn = t[l] + s[l]; }
+        if (sh > 24) { sh = 24; tn = t[l] + s[l] - 24; }
+        shift[l] = sh;
+        t[l + 1] = tn;
+    }
+    int32_t out_exp = std::max(-30, std::min(60, t[4] + s[4]));
+    return upload_int_network(g, q.data(), shift, out_exp);
+}
+
+}  // namespace
+
+extern "C" rp_status rp_guide_create(const float *box, uint32_t batch, uint64_t seed, rp_guide **out) {
+    if (!box || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (batch < 256 || (batch & 1u) || batch > (1u << 24))
+        return fail(RP_ERR_INVALID_ARG, "batch must be even and in [256, 2^24]");
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(box[i])) return fail(RP_ERR_INVALID_ARG, "box must be finite");
+    if (rp_status s = need_device()) return s;
+    rp_guide *g = new rp_guide_s();
+    for (int i = 0; i < 6; ++i) g->box[i] = box[i];
+    g->cap = batch;
+    const size_t C = batch;
+    rp_status st = RP_OK;
+#define GA_(ptr, bytes) if (st == RP_OK) st = guide_alloc(g, (void **)&(ptr), (bytes));
+    GA_(g->Wm, sizeof(float) * kGWeights) GA_(g->m, sizeof(float) * kGWeights)
+    GA_(g->v, sizeof(float) * kGWeights) GA_(g->grad, sizeof(float) * kGWeights)
+    GA_(g->loss, sizeof(float)) GA_(g->wsum, sizeof(float)) GA_(g->d_box, sizeof(float) * 6)
+    GA_(g->amax, sizeof(unsigned int) * 4) GA_(g->err, sizeof(int))
+    GA_(g->Wbf, sizeof(__nv_bfloat16) * kGWeights) GA_(g->Wq, sizeof(__nv_bfloat16) * kGWeights)
+    GA_(g->smp.p, sizeof(float) * 3 * C) GA_(g->smp.n, sizeof(float) * 3 * C)
+    GA_(g->smp.w, sizeof(float) * 3 * C) GA_(g->smp.wt, sizeof(float) * C)
+    GA_(g->X, sizeof(__nv_bfloat16) * kGIn * C) GA_(g->omega, sizeof(float) * 3 * C)
+    GA_(g->wt, sizeof(float) * C)
+#undef GA_
+    g->smp.cap = batch;
+    if (st == RP_OK && cudaMemcpy(g->d_box, box, sizeof(float) * 6, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(RP_ERR_CUDA, "upload box");
+    if (st == RP_OK) {
+        std::vector<float> W(kGWeights);
+        uint64_t rs = seed;
+        for (int l = 0; l < kGLayers; ++l) {
+            const double sd = std::sqrt(2.0 / guide_in(l));
+            for (int i = guide_off(l); i < guide_off(l + 1); ++i) {
+                const double a = unit_open(rs), b = unit_open(rs);
+                W[i] = (float)(sd * std::sqrt(-2.0 * std::log(a)) * std::cos(6.283185307179586 * b));
+            }
+        }
+        st = upload_float_weights(g, W.data());
+    }
+    if (st != RP_OK) {
+        delete g;
+        return st;
+    }
+    *out = g;
+    return RP_OK;
+}
+
+extern "C" void rp_guide_destroy(rp_guide *guide) { delete guide; }
+
+extern "C" rp_status rp_guide_set_weights(rp_guide *g, const float *W) {
+    if (!g || !W) return fail(RP_ERR_INVALID_ARG, "null argument");
+    for (int i = 0; i < kGWeights; ++i)
+        if (!std::isfinite(W[i])) return fail(RP_ERR_INVALID_ARG, "weights must be finite");
+    return upload_float_weights(g, W);
+}
+
+extern "C" rp_status rp_guide_get_weights(rp_guide *g, float *W) {
+    if (!g || !W) return fail(RP_ERR_INVALID_ARG, "null argument");
+    RP_CUDA(cudaDeviceSynchronize(), "sync");
+    RP_CUDA(cudaMemcpy(W, g->Wm, sizeof(float) * kGWeights, cudaMemcpyDeviceToHost), "download");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_guide_set_int(rp_guide *g, const int8_t *W, const int32_t *shift,
+                                      int32_t out_exp) {
+    if (!g || !W || !shift) return fail(RP_ERR_INVALID_ARG, "null argument");
+    return upload_int_network(g, W, shift, out_exp);
+}
+
+extern "C" rp_status rp_guide_get_int(rp_guide *g, int8_t *W, int32_t *shift, int32_t *out_exp) {
+    if (!g || !W || !shift || !out_exp) return fail(RP_ERR_INVALID_ARG, "null argument");
+    if (!g->has_int) return fail(RP_ERR_INVALID_ARG, "the guide has no integer network yet");
+    std::vector<__nv_bfloat16> q(kGWeights);
+    RP_CUDA(cudaDeviceSynchronize(), "sync");
+    RP_CUDA(cudaMemcpy(q.data(), g->Wq, sizeof(__nv_bfloat16) * kGWeights, cudaMemcpyDeviceToHost),
+            "download");
+    for (int i = 0; i < kGWeights; ++i) W[i] = (int8_t)(int)__bfloat162float(q[i]);
+    for (int l = 0; l < 4; ++l) shift[l] = g->shift[l];
+    *out_exp = g->out_exp;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_guide_infer(rp_guide *g, const int8_t *d_in, uint32_t n, float *d_out,
+                                    void *stream) {
+    if (!g || (n && (!d_in || !d_out))) return fail(RP_ERR_INVALID_ARG, "null argument");
+    if (!g->has_int) return fail(RP_ERR_INVALID_ARG, "the guide has no integer network yet");
+    GuideNet net{};
+    net.Wq = g->Wq;
+    for (int l = 0; l < 4; ++l) net.hid_scale[l] = std::ldexp(1.0f, -g->shift[l]);
+    net.out_scale = std::ldexp(1.0f, -g->out_exp);
+    for (int i = 0; i < 6; ++i) net.box[i] = g->box[i];
+    RP_CUDA(launch_guide_infer(net, d_in, n, d_out, g->err, (cudaStream_t)stream), "guide inference");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_guide_loss_grad(rp_guide *g, const float *d_x, const float *d_omega,
+                                        const float *d_wt, uint32_t n, float *d_grad, float *d_loss,
+                                        void *stream) {
+    if (!g || !d_grad || !d_loss || (n && (!d_x || !d_omega || !d_wt)))
+        return fail(RP_ERR_INVALID_ARG, "null argument");
+    if (n == 0) return RP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->xs_rows < n) {
+        if (g->Xs) cudaFree(g->Xs);
+        g->Xs = nullptr;
+        g->xs_rows = 0;
+        cudaError_t e = cudaMalloc((void **)&g->Xs, sizeof(__nv_bfloat16) * kGIn * (size_t)n);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc features");
+        g->xs_rows = n;
+    }
+    RP_CUDA(launch_f32_to_bf16(d_x, g->Xs, (size_t)kGIn * n, st), "convert features");
+    GuideTrain T{};
+    T.W = g->Wbf;
+    T.X = g->Xs;
+    T.omega = d_omega;
+    T.wt = d_wt;
+    T.n = n;
+    T.inv_n = 1.0f / (float)n;
+    T.wsum = nullptr;
+    T.grad = d_grad;
+    T.loss = d_loss;
+    T.amax = g->amax;
+    T.err = g->err;
+    RP_CUDA(launch_guide_train(T, st), "guide training kernel");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_guide_train_step(rp_guide *g, float lr, float *loss_out, void *stream) {
+    if (!g) return fail(RP_ERR_INVALID_ARG, "null guide");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return fail(RP_ERR_INVALID_ARG, "lr must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t n = g->cap;
+    RP_CUDA(launch_guide_features(g->smp, g->d_box, n, g->X, g->omega, g->wt, g->wsum, st),
+            "guide features");
+    RP_CUDA(cudaMemsetAsync(g->grad, 0, sizeof(float) * kGWeights, st), "memset");
+    RP_CUDA(cudaMemsetAsync(g->loss, 0, sizeof(float), st), "memset");
+    RP_CUDA(cudaMemsetAsync(g->amax, 0, sizeof(unsigned int) * 4, st), "memset");
+    GuideTrain T{};
+    T.W = g->Wbf;
+    T.X = g->X;
+    T.omega = g->omega;
+    T.wt = g->wt;
+    T.n = n;
+    T.inv_n = 1.0f / (float)n;
+    T.wsum = g->wsum;          // the loss is the weighted mean -sum wt log q / sum wt
+    T.grad = g->grad;
+    T.loss = g->loss;
+    T.amax = g->amax;
+    T.err = g->err;
+    RP_CUDA(launch_guide_train(T, st), "guide training kernel");
+    g->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.99f;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)g->adam_t));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)g->adam_t));
+    RP_CUDA(launch_guide_adam(g->Wm, g->m, g->v, g->grad, g->Wbf, kGWeights, lr, b1, b2, 1e-8f, c1, c2, st),
+            "adam");
+    RP_CUDA(cudaStreamSynchronize(st), "training step");
+    int err = 0;
+    float loss = 0.f, amax[4];
+    unsigned int ab[4];
+    RP_CUDA(cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (err) return fail(RP_ERR_TIMEOUT, "a tensor-core wait of the guide kernels timed out");
+    RP_CUDA(cudaMemcpy(&loss, g->loss, sizeof(float), cudaMemcpyDeviceToHost), "read loss");
+    RP_CUDA(cudaMemcpy(ab, g->amax, sizeof ab, cudaMemcpyDeviceToHost), "read maxima");
+    for (int l = 0; l < 4; ++l) std::memcpy(&amax[l], &ab[l], sizeof(float));
+    if (loss_out) *loss_out = loss;
+    std::vector<float> W(kGWeights);
+    RP_CUDA(cudaMemcpy(W.data(), g->Wm, sizeof(float) * kGWeights, cudaMemcpyDeviceToHost), "download");
+    return quantize(g, W.data(), amax);
+}
+
+extern "C" rp_status rp_guide_status(rp_guide *g) {
+    if (!g) return fail(RP_ERR_INVALID_ARG, "null guide");
+    int err = 0;
+    RP_CUDA(cudaDeviceSynchronize(), "sync");
+    RP_CUDA(cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    return err ? fail(RP_ERR_TIMEOUT, "a tensor-core wait of the guide kernels timed out") : RP_OK;
+}
+
+extern "C" rp_status rp_scene_set_guide(rp_scene *scene, rp_guide *guide) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    scene->guide = guide;
+    if (!guide) scene->free_guide_buffers();
+    return RP_OK;
+}

@@ -994,6 +994,20 @@ static __device__ __forceinline__ void splat(double *img, int pix, float3 v) {
 static __device__ void emit(Ctx &c, uint32_t root, int tech, int g, int sa, int sb, int pa, float3 va,
                      int pb, float3 vb, int status, float Pg, float Py, float J) {
     const LaunchArgs &A = c.A;
+    if (tech == T_3 && A.G.on) {
+        // learned proposal: the root's light-side direction was drawn from
+        // q = p_cos / 2 + mixture / 2, so its values carry p_cos / q; the
+        // magnitude of what the root adds is its training weight
+        if (A.G.use_net) {
+            const float s = A.G.gratio[root - A.root_begin];
+            va = va * s;
+            vb = vb * s;
+        }
+        const uint32_t slot = root < A.G.half ? (uint32_t)(g - 1) * A.G.half + root : ~0u;
+        if (slot != ~0u)
+            atomicAdd(A.G.smp.wt + slot, fabsf(va.x) + fabsf(va.y) + fabsf(va.z) + fabsf(vb.x) +
+                                             fabsf(vb.y) + fabsf(vb.z));
+    }
     if (A.rec_count) {
         unsigned long long idx = atomicAdd(A.rec_count, 1ull);
         if (A.rec && idx < A.rec_cap) {

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "guide.h"
 #include "rp_wave.h"
 
 namespace rp {
@@ -86,6 +87,19 @@ struct KernelTimer {
 };
 
 
+// learned proposal of technique (3) during a render
+struct GuideLaunch {
+    int on;                     // training samples of technique (3) are collected
+    int use_net;                // technique (3) draws its light-side direction from the network
+    GuideNet net;
+    int8_t *gin;                // [R][80] integer input features (wave-local roots)
+    float *gout;                // [R][48] network outputs
+    float *gratio;              // [R] p_cos / q of the drawn direction
+    GuideSamples smp;           // training samples; frame g, root r < half at (g - 1) half + r
+    uint32_t half;
+    int *err;                   // tensor-core wait timeout flag
+};
+
 struct LaunchArgs {
     DevScene S;
     DevEdit E;
@@ -102,6 +116,7 @@ struct LaunchArgs {
     WaveBuf W;                  // wavefront buffers (wavefront mode)
     int residual;               // 1: residual techniques, 0: primal path tracing
     KernelTimer *timer;         // host only: per-kernel event timing, or null
+    GuideLaunch G;              // learned proposal (G.on = 0: none)
 };
 
 // launchers implemented in the .cu files

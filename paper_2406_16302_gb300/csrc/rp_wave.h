@@ -31,7 +31,7 @@ __host__ __device__ __forceinline__ int tag_step(uint32_t t) { return (int)((t >
 enum { CK_CAMERA = 0, CK_NEE = 1, CK_GHOST_WALK = 2, CK_GHOST_NEE = 3 };
 
 // per-root flag bits
-enum { RF_ROOT_OK = 1 };
+enum { RF_ROOT_OK = 1, RF_GUIDE = 2 };
 
 constexpr int kMaxIter = 16;      // counter slots per queue
 

@@ -67,7 +67,12 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
            "rp_render_residual_host",
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
            "rp_enable_stats", "rp_get_stats", "rp_enable_timing", "rp_get_kernel_times",
+           "rp_guide_create", "rp_guide_destroy", "rp_guide_set_weights", "rp_guide_get_weights",
+           "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_loss_grad",
+           "rp_guide_train_step", "rp_guide_status", "rp_scene_set_guide",
            "rp_last_error"]
+
+GUIDE_WEIGHTS, GUIDE_IN, GUIDE_OUT = 20480, 80, 48
 
 _lib = None
 
@@ -99,6 +104,17 @@ def lib():
         "rp_get_stats": (I, [P, P]),
         "rp_enable_timing": (I, [P, I]),
         "rp_get_kernel_times": (I, [P, P, I, P]),
+        "rp_guide_create": (I, [P, U32, U64, P]),
+        "rp_guide_destroy": (None, [P]),
+        "rp_guide_set_weights": (I, [P, P]),
+        "rp_guide_get_weights": (I, [P, P]),
+        "rp_guide_set_int": (I, [P, P, P, C.c_int32]),
+        "rp_guide_get_int": (I, [P, P, P, P]),
+        "rp_guide_infer": (I, [P, P, U32, P, P]),
+        "rp_guide_loss_grad": (I, [P, P, P, P, U32, P, P, P]),
+        "rp_guide_train_step": (I, [P, C.c_float, P, P]),
+        "rp_guide_status": (I, [P]),
+        "rp_scene_set_guide": (I, [P, P]),
         "rp_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -283,6 +299,83 @@ def rp_get_kernel_times(scene: Scene) -> dict:
     _check(lib().rp_get_kernel_times(scene.h, arr, cap, C.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms))
             for i in range(min(n.value, cap))}
+
+
+class Guide:
+    """rp_guide_create / rp_guide_destroy: the learned proposal of technique (3)."""
+
+    def __init__(self, box, batch=1 << 20, seed=1):
+        b = np.ascontiguousarray(box, dtype=np.float32)
+        h = C.c_void_p()
+        _check(lib().rp_guide_create(b.ctypes.data_as(C.c_void_p), int(batch), int(seed),
+                                     C.byref(h)))
+        self.h = h
+        self.batch = int(batch)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rp_guide_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rp_guide_set_weights(guide: Guide, W):
+    w = np.ascontiguousarray(W, dtype=np.float32)
+    assert w.size == GUIDE_WEIGHTS
+    _check(lib().rp_guide_set_weights(guide.h, w.ctypes.data_as(C.c_void_p)))
+
+
+def rp_guide_get_weights(guide: Guide):
+    w = np.zeros(GUIDE_WEIGHTS, dtype=np.float32)
+    _check(lib().rp_guide_get_weights(guide.h, w.ctypes.data_as(C.c_void_p)))
+    return w
+
+
+def rp_guide_set_int(guide: Guide, W, shift, out_exp):
+    w = np.ascontiguousarray(W, dtype=np.int8)
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    assert w.size == GUIDE_WEIGHTS and sh.size == 4
+    _check(lib().rp_guide_set_int(guide.h, w.ctypes.data_as(C.c_void_p),
+                                  sh.ctypes.data_as(C.c_void_p), int(out_exp)))
+
+
+def rp_guide_get_int(guide: Guide):
+    w = np.zeros(GUIDE_WEIGHTS, dtype=np.int8)
+    sh = np.zeros(4, dtype=np.int32)
+    e = C.c_int32()
+    _check(lib().rp_guide_get_int(guide.h, w.ctypes.data_as(C.c_void_p),
+                                  sh.ctypes.data_as(C.c_void_p), C.byref(e)))
+    return w, sh, int(e.value)
+
+
+def rp_guide_infer(guide: Guide, m_in, out, stream=None):
+    """m_in: int8 tensor [n][80] on the device; out: float32 tensor [n][48]."""
+    _check(lib().rp_guide_infer(guide.h, _ptr(m_in), m_in.shape[0], _ptr(out), _stream(stream)))
+
+
+def rp_guide_loss_grad(guide: Guide, x, omega, wt, grad, loss, stream=None):
+    """Adds the float network's mean loss and its weight gradient into loss / grad."""
+    _check(lib().rp_guide_loss_grad(guide.h, _ptr(x), _ptr(omega), _ptr(wt), x.shape[0],
+                                    _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def rp_guide_train_step(guide: Guide, lr=2e-3, stream=None):
+    loss = C.c_float()
+    _check(lib().rp_guide_train_step(guide.h, float(lr), C.byref(loss), _stream(stream)))
+    return float(loss.value)
+
+
+def rp_guide_status(guide: Guide):
+    _check(lib().rp_guide_status(guide.h))
+
+
+def rp_scene_set_guide(scene: Scene, guide):
+    _check(lib().rp_scene_set_guide(scene.h, None if guide is None else guide.h))
 
 
 # ---------------------------------------------------------------------------

@@ -390,6 +390,32 @@ def cfg2_box_blob(width=256, height=256, max_depth=8, blob_level=5):
     return scene, edit
 
 
+def box_blob_side_light(width=64, height=64, max_depth=8, blob_level=4, radiance=60.0):
+    """The cfg2 box and material edit with the ceiling light replaced by a small
+    quad light (0.3 x 0.3) that faces the back wall from 0.15 in front of it:
+    the blob receives no direct light, only light from the lit wall patch and
+    further bounces -- indirect illumination concentrated in a few directions."""
+    mb = MeshBuilder(); mats = []
+    _box_room(mb, mats, light=False)
+    sph = len(mats); mats.append(material(LAMBERT, (0.8, 0.8, 0.8)))
+    sv, stt = icosphere(3)
+    mb.add(sv * 0.35 + np.array([-0.3, -0.64, -0.2]), stt, sph)
+    lm = len(mats); mats.append(material(LAMBERT, (0, 0, 0), emission=(radiance,) * 3))
+    qv, qt = quad((0.45, 0.35, -0.85), (0.15, 0, 0), (0, -0.15, 0))      # normal -z
+    mb.add(qv, qt, lm)
+    s_v, s_t, s_m = mb.arrays()
+    bv, bt = displaced_icosphere(blob_level, 0.3, 0.1, seed=2406)
+    c = np.array([0.35, -0.65, 0.1])
+    scene = Scene(s_v, s_t, s_m, bv.astype(np.float32), bt.astype(np.uint32),
+                  np.stack(mats), _box_camera(width, height), max_depth,
+                  d_min=0.01 * 2.0 * math.sqrt(3.0), name="box_blob_side_light")
+    M = translate(c)
+    edit = Edit(M, M.copy(), material(LAMBERT, (0.8, 0.8, 0.8)),
+                material(GGX, (0, 0, 0), alpha=0.3, f0=(0.04, 0.04, 0.04)),
+                name="lambert_to_ggx")
+    return scene, edit
+
+
 def cfg3_terrain(width=1024, height=1024, max_depth=8, grid=708, n_instances=200,
                  seed=2406):
     """Terrain at scale: a grid x grid fBm height field (2 * grid^2 triangles),

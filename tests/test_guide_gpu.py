@@ -1,0 +1,194 @@
+"""The learned proposal on the GPU, through the C ABI, against the oracle:
+integer inference bit-exact, the training kernel's loss gradient within the
+BF16 tolerance of the FP64 gradient, guided technique (3) per sample, and
+what a trained network gains over the plain technique."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2406_16302_gb300 import scenes as S
+from test_gpu_parity import Tally, _compare
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-2            # relative (norm) error of BF16 products with FP32 accumulation
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2406_16302_gb300 import build, rp as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def _int_guide(seed, box):
+    return S.random_int_guide(seed, box)
+
+
+@pytest.mark.parametrize("n", [1, 128, 129, 1037, 40000])
+def test_integer_inference_is_exact(rp, n):
+    import torch
+    box = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    W, sh, oe, _ = _int_guide(3, box)
+    g = rp.Guide(box, batch=256)
+    rp.rp_guide_set_int(g, W, sh, oe)
+    rng = np.random.default_rng(n)
+    m = rng.integers(-127, 128, size=(n, 80)).astype(np.int8)
+    m[:, 78] = 127
+    m[:, 79] = 0
+    d_in = torch.from_numpy(m).cuda()
+    d_out = torch.full((n, 48), float("nan"), device="cuda")
+    rp.rp_guide_infer(g, d_in, d_out)
+    torch.cuda.synchronize()
+    rp.rp_guide_status(g)
+    got = d_out.cpu().numpy().astype(np.float64)
+    want = O.guide_forward(W, sh, oe, m.astype(np.int32))
+    assert np.array_equal(got, want), (np.argwhere(got != want)[:5], got.ravel()[:5], want.ravel()[:5])
+
+
+def test_integer_inference_of_encoded_points(rp):
+    """Features from the oracle's encoding of object-space points, then the
+    network: every output equal."""
+    import torch
+    scene, _ = S.cfg2_box_blob(width=8, height=8, blob_level=3)
+    box = S.guide_box(scene.dyn_vertices)
+    W, sh, oe, _ = _int_guide(7, box)
+    g = rp.Guide(box, batch=256)
+    rp.rp_guide_set_int(g, W, sh, oe)
+    rng = np.random.default_rng(1)
+    v = np.asarray(scene.dyn_vertices, np.float64)
+    pts = v[rng.integers(0, len(v), size=300)]
+    nrm = rng.normal(size=(300, 3)); nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    m = np.array([O.guide_encode(box, p, q) for p, q in zip(pts, nrm)], np.int32)
+    d_out = torch.zeros((300, 48), device="cuda")
+    rp.rp_guide_infer(g, torch.from_numpy(m.astype(np.int8)).cuda(), d_out)
+    assert np.array_equal(d_out.cpu().numpy().astype(np.float64), O.guide_forward(W, sh, oe, m))
+
+
+@pytest.mark.parametrize("rows", [200, 1000])
+def test_training_gradient_matches_oracle(rp, rows):
+    """Loss and weight gradient of the float network: BF16 tensor-core
+    forward and backward (FP32 accumulation) against FP64 back-propagation on
+    the same BF16-valued weights and features."""
+    import torch
+    box = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    g = rp.Guide(box, batch=256)
+    W = S.random_float_guide(11, gain=0.9)
+    rp.rp_guide_set_weights(g, W.astype(np.float32))
+    rng = np.random.default_rng(rows)
+    x = S.bf16_round(rng.uniform(-1, 1, size=(rows, 80)).astype(np.float32))
+    x[:, 78] = 127 / 128
+    x[:, 79] = 0
+    om = rng.normal(size=(rows, 3)); om /= np.linalg.norm(om, axis=1, keepdims=True)
+    wt = rng.uniform(0.1, 2.0, size=rows)
+    wt[::7] = 0.0                                  # rows that add nothing
+    grad = torch.zeros(20480, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    rp.rp_guide_loss_grad(g, torch.from_numpy(x).cuda(),
+                          torch.from_numpy(om.astype(np.float32)).cuda(),
+                          torch.from_numpy(wt.astype(np.float32)).cuda(), grad, loss)
+    torch.cuda.synchronize()
+    rp.rp_guide_status(g)
+    want_loss, want = O.mlp_loss_grad(W, x.astype(np.float64), om.astype(np.float32).astype(np.float64),
+                                      wt.astype(np.float32).astype(np.float64))
+    got = grad.cpu().numpy().astype(np.float64)
+    offs = [0, 5120, 9216, 13312, 17408, 20480]
+    errs = [np.linalg.norm(got[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-30)
+            for a, b in zip(offs, offs[1:])]
+    print("loss", float(loss.item()), want_loss, "layer errors", errs)
+    assert abs(float(loss.item()) - want_loss) <= GRAD_TOL * abs(want_loss)
+    assert max(errs) <= GRAD_TOL, errs
+
+
+GUIDED = [
+    ("cfg1_box_sphere", {"width": 32, "height": 32, "max_depth": 6}, 4),     # motion
+    ("cfg2_box_blob", {"width": 32, "height": 32, "max_depth": 6, "blob_level": 4}, 4),  # material
+]
+
+
+@pytest.mark.parametrize("builder,kw,spp", GUIDED)
+def test_guided_technique_three_matches_oracle(rp, builder, kw, spp):
+    scene, edit = getattr(S, builder)(**kw)
+    box = S.guide_box(scene.dyn_vertices)
+    net = _int_guide(3, box)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    g = rp.Guide(box, batch=1024)
+    rp.rp_guide_set_int(g, net[0].astype(np.int8), net[1], net[2])
+    rp.rp_scene_set_guide(sc, g)
+    ora = O.Oracle(scene, edit)
+    ora.set_guide(net)
+    N = sc.n_roots(spp)
+    tally = Tally()
+    for tech in (3, 1, 7):
+        for frame in (1, 2):
+            gpu = rp.dump_samples(sc, ed, tech, frame, spp, 21, 0, N)
+            ref = ora.dump(tech, frame, spp, 21, 0, N)
+            frac, n, bad = _compare(gpu, ref)
+            tally.add(frac, n, bad, (builder, tech, frame))
+    tally.check()
+    rp.rp_guide_status(g)
+
+
+def test_guided_render_equals_sum_of_records(rp):
+    """The splatted image of a guided render is the sum of its records
+    (values carry p_cos / q in both)."""
+    import torch
+    scene, edit = S.cfg2_box_blob(width=16, height=16, max_depth=6, blob_level=3)
+    box = S.guide_box(scene.dyn_vertices)
+    net = _int_guide(5, box)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    g = rp.Guide(box, batch=512)
+    rp.rp_guide_set_int(g, net[0].astype(np.int8), net[1], net[2])
+    rp.rp_scene_set_guide(sc, g)
+    spp = 8
+    img = rp.render_residual(sc, ed, spp, 5, tech_mask=4).cpu().numpy()
+    acc = np.zeros(sc.shape)
+    for frame in (1, 2):
+        rec = rp.dump_samples(sc, ed, 3, frame, spp, 5, 0, sc.n_roots(spp), tech_mask=4)
+        for r in rec:
+            if r["pix_a"] >= 0:
+                acc.reshape(-1, 3)[r["pix_a"]] += r["va"]
+            if r["pix_b"] >= 0:
+                acc.reshape(-1, 3)[r["pix_b"]] += r["vb"]
+    assert np.allclose(img, acc, rtol=1e-4, atol=1e-7 * np.abs(acc).max())
+
+
+def _variance(rp, sc, ed, spp, seeds, mask):
+    ims = np.array([rp.render_residual(sc, ed, spp, s, tech_mask=mask).cpu().numpy() for s in seeds])
+    return ims.mean(0), ims.var(0, ddof=1)
+
+
+def test_training_lowers_loss_and_variance(rp):
+    """Online training on the method's own samples, in a box whose object is
+    lit only indirectly (a small light facing the back wall): the weighted
+    loss falls, and technique (3) with the trained network estimates the same
+    image as cosine sampling with lower variance at the same sample count."""
+    scene, edit = S.box_blob_side_light(width=64, height=64, max_depth=8, blob_level=4)
+    box = S.guide_box(scene.dyn_vertices)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    g = rp.Guide(box, batch=1 << 16, seed=3)
+    rp.rp_scene_set_guide(sc, g)
+    spp = 16
+    losses = []
+    for it in range(40):
+        rp.render_residual(sc, ed, spp, 1000 + it, tech_mask=4)
+        losses.append(rp.rp_guide_train_step(g, lr=1e-2))
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-5:]) < 0.8 * np.mean(losses[:5]), losses
+    K = 16
+    m_g, v_g = _variance(rp, sc, ed, spp, range(2000, 2000 + K), 4)
+    rp.rp_scene_set_guide(sc, None)
+    m_p, v_p = _variance(rp, sc, ed, spp, range(3000, 3000 + K), 4)
+    zs = (m_g - m_p).sum() / np.sqrt(((v_g + v_p) / K).sum())
+    z = (m_g - m_p) / (np.sqrt((v_g + v_p) / K) + 1e-30)
+    ratio = v_g.sum() / v_p.sum()
+    print("variance ratio guided / cosine:", ratio, "z", zs, "losses", losses[:3], losses[-3:])
+    assert abs(zs) < 4.0, zs
+    assert np.sqrt((z ** 2).mean()) < 1.5
+    assert ratio < 0.8, ratio
