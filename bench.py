@@ -76,7 +76,109 @@ def workload(name):
     if name == "terrain_motion_1024":
         scene, edit = scenes.cfg3_terrain()
         return scene, edit, 16
+    if name == "box_blob_side_light_256":
+        scene, edit = scenes.box_blob_side_light(width=256, height=256, max_depth=8, blob_level=5)
+        return scene, edit, 64
     raise SystemExit(f"unknown workload {name}")
+
+
+def equal_time_mse(rp, sc, ed, scene, spp, K=4, ref_renders=16, guide_iters=30, guide_lr=1e-2):
+    """Equal-time residual MSE against a converged reference (the plain
+    method at ref_renders x 4 x spp, averaged over independent seeds).  Each
+    method runs K times at its own sample count; its MSE is brought to the
+    plain method's time T by MSE(T) = MSE(t) t / T (Monte Carlo variance
+    falls as 1 / time).  Methods: the plain residual estimator; the same with
+    the learned proposal after guide_iters online training iterations (the
+    training time reported beside it); re-rendering frame 2 by path tracing
+    against a converged frame 1; correlated path tracing (both frames with
+    the same numbers)."""
+    import torch
+    from paper_2406_16302_gb300 import scenes
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def residual(s, seed):
+        out = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+        return out, timed(lambda: rp.rp_render_residual(sc, ed, s, seed, out, stream=stream))
+
+    def primal(frame, s, seed):
+        out = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+        return out, timed(lambda: rp.rp_render_primal(sc, ed, frame, s, seed, out, stream=stream))
+
+    ref = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+    for i in range(ref_renders):
+        ref += residual(4 * spp, 700000 + i)[0]
+    ref /= ref_renders
+
+    def mse(img):
+        return float(((img - ref) ** 2).mean().item())
+
+    out = {"reference": f"plain residual, {ref_renders} x {4 * spp} spp averaged",
+           "spp": spp, "repeats": K}
+    # plain method
+    ms, ts = [], []
+    for k in range(K):
+        img, t = residual(spp, 710000 + k)
+        ms.append(mse(img)); ts.append(t)
+    T = float(np.mean(ts))
+    out["budget_ms"] = T
+    out["plain"] = {"mse": float(np.mean(ms)), "ms": T, "mse_at_budget": float(np.mean(ms))}
+    # path tracing re-render of frame 2 against a converged frame 1
+    _, t1 = primal(2, spp, 720000)
+    s_pt = max(1, int(round(spp * T / t1)))
+    I1 = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+    for i in range(ref_renders):
+        I1 += primal(1, 4 * spp, 730000 + i)[0]
+    I1 /= ref_renders
+    ms, ts = [], []
+    for k in range(K):
+        img, t = primal(2, s_pt, 740000 + k)
+        ms.append(mse(img - I1)); ts.append(t)
+    out["pt_rerender"] = {"spp": s_pt, "mse": float(np.mean(ms)), "ms": float(np.mean(ts)),
+                          "mse_at_budget": float(np.mean(ms)) * float(np.mean(ts)) / T}
+    # correlated path tracing: both frames with the same numbers
+    s_c = max(1, s_pt // 2)
+    ms, ts = [], []
+    for k in range(K):
+        i2, ta = primal(2, s_c, 750000 + k)
+        i1, tb = primal(1, s_c, 750000 + k)
+        ms.append(mse(i2 - i1)); ts.append(ta + tb)
+    out["correlated_pt"] = {"spp": s_c, "mse": float(np.mean(ms)), "ms": float(np.mean(ts)),
+                            "mse_at_budget": float(np.mean(ms)) * float(np.mean(ts)) / T}
+    # learned proposal, trained online on the method's own samples
+    box = scenes.guide_box(scene.dyn_vertices)
+    batch = 1 << 20
+    guide = rp.Guide(box, batch=batch, seed=1)
+    rp.rp_scene_set_guide(sc, guide)
+    s_train = max(1, (batch // 2 + sc.width * sc.height - 1) // (sc.width * sc.height))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for i in range(guide_iters):
+        residual(s_train, 760000 + i)
+        losses.append(rp.rp_guide_train_step(guide, lr=guide_lr))
+    train_s = time.perf_counter() - t0
+    ms, ts = [], []
+    for k in range(K):
+        img, t = residual(spp, 770000 + k)
+        ms.append(mse(img)); ts.append(t)
+    rp.rp_scene_set_guide(sc, None)
+    out["guided"] = {"mse": float(np.mean(ms)), "ms": float(np.mean(ts)),
+                     "mse_at_budget": float(np.mean(ms)) * float(np.mean(ts)) / T,
+                     "training": {"iterations": guide_iters, "spp_per_iteration": s_train,
+                                  "batch": batch, "seconds": train_s,
+                                  "loss_first_last": [losses[0], losses[-1]]}}
+    out["ratios_at_budget"] = {k: out[k]["mse_at_budget"] / out["plain"]["mse_at_budget"]
+                               for k in ("guided", "pt_rerender", "correlated_pt")}
+    return out
 
 
 def dist_env():
@@ -218,6 +320,7 @@ def main():
     ap.add_argument("--workload", default="box_blob_material_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE comparison")
     ap.add_argument("--spp", type=int, default=None, help="override the workload's spp "
                     "(smaller cases for profiling; not a benchmark number)")
     args = ap.parse_args()
@@ -369,6 +472,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(scene, edit, spp)
+    et_mse = None
+    if not args.no_mse and ws == 1:
+        et_mse = equal_time_mse(rp, sc, ed, scene, spp)
     line = {
         "metric": "residual samples/s", "value": value, "unit": "residual samples/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": worst_ms,
@@ -383,7 +489,7 @@ def main():
                    "per_kernel": per_kernel,
                    "rays_per_step": work["rays_closest"] + work["rays_shadow"],
                    "paths_per_step": work["paths"]},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "equal_time_mse": et_mse,
         "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clock,
     }
     print(json.dumps(line), flush=True)

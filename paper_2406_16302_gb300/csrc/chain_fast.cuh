@@ -76,6 +76,20 @@ struct Light {
     float Py[2][kSide], B[2][kSide];
 };
 
+// Power-of-two rescaling of running products.  Near-coincident walk
+// vertices make geometric terms and area densities of 1e8 and more per edge,
+// so the products overflow single precision over a long walk.  Every value
+// f(t, s) and every denominator P(t, s) is linear in the eye-side running
+// state (E, A, Pz) and in the light-side running state (L, Py, B), so each
+// side may be scaled by a common factor 2^e at any step (the same in both
+// frames, whose sums Pg + Py share it) without changing f / P.
+__device__ __forceinline__ int rescale_exp(float mx) {
+    if (!(mx > 0x1p40f) && !(mx > 0.f && mx < 0x1p-40f)) return 0;
+    int e;
+    frexpf(mx, &e);
+    return -e;
+}
+
 }  // namespace fast_detail
 
 // splat one no-motion path (fx, Pg: base frame; fy, Py: other frame)
@@ -115,6 +129,7 @@ __device__ void fast_eye(const Ctx &cx, int nf, const int *frames, const Vtx *z,
     const DevScene &Sc = cx.A.S;
     const Vtx camv = camera_vertex(cx);
     const float pD = 1.0f / Sc.dyn_area;
+    int sh[kSide + 1];                  // rescaling exponents, chosen in the first frame
     for (int f = 0; f < nf; ++f) {
         float3 prho = f3(1.f, 1.f, 1.f);
         float Pf = 1.f, Pz = 1.f, Sz = 0.f;
@@ -141,6 +156,13 @@ __device__ void fast_eye(const Ctx &cx, int nf, const int *frames, const Vtx *z,
                 prho = mul3(prho, rho3(mm, zn, zm, zp)) * G;
                 Pf *= pdf3(mm, zn, zm, zp);
                 Pz *= pLI;
+                if (f == 0)
+                    sh[m] = rescale_exp(fmaxf(fmaxf(fmaxf(prho.x, prho.y), fmaxf(prho.z, Pf)),
+                                              fmaxf(Pz, Sz)));
+                if (sh[m]) {
+                    const float sc = ldexpf(1.f, sh[m]);
+                    prho = prho * sc; Pf *= sc; Pz *= sc; Sz *= sc;
+                }
             }
         }
     }
@@ -154,6 +176,7 @@ __device__ void fast_light(const Ctx &cx, int nf, const int *frames, const Vtx *
     using namespace fast_detail;
     const DevScene &Sc = cx.A.S;
     const float pD = 1.0f / Sc.dyn_area;
+    int sh[kSide + 1];                  // rescaling exponents, chosen in the first frame
     for (int f = 0; f < nf; ++f) {
         float3 prho = f3(1.f, 1.f, 1.f);
         float Py = 1.f, PLy = 1.f, Sy = 0.f;
@@ -178,6 +201,13 @@ __device__ void fast_light(const Ctx &cx, int nf, const int *frames, const Vtx *
                 if (dyn) Sy += area_from_dir(cosine_pdf(ym.n, unit3(yn.p - ym.p)), ym.p, yn) * PLy;
                 prho = mul3(prho, rho3(mm, yp, ym, yn)) * G2(ym, yn);
                 Py *= pEI;
+                if (f == 0)
+                    sh[m] = rescale_exp(fmaxf(fmaxf(fmaxf(prho.x, prho.y), fmaxf(prho.z, Py)),
+                                              fmaxf(PLy, Sy)));
+                if (sh[m]) {
+                    const float sc = ldexpf(1.f, sh[m]);
+                    prho = prho * sc; Py *= sc; PLy *= sc; Sy *= sc;
+                }
             }
         }
     }
@@ -357,6 +387,17 @@ __device__ void fast_pt(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *x, co
                     if (dj) S3[f] += area_from_dir(cosine_pdf(xj.n, unit3(xn.p - xj.p)), xj.p, xn) * PL[f];
                 }
                 PE[f] *= pE;
+            }
+            float mx = 0.f;
+            for (int f = 0; f < nf; ++f)
+                mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(R[f].x, R[f].y), fmaxf(R[f].z, PE[f])),
+                                     fmaxf(PL[f], S3[f])));
+            const int e = fast_detail::rescale_exp(mx);
+            if (e) {
+                const float sc = ldexpf(1.f, e);
+                for (int f = 0; f < nf; ++f) {
+                    R[f] = R[f] * sc; PE[f] *= sc; PL[f] *= sc; S3[f] *= sc;
+                }
             }
         }
     }

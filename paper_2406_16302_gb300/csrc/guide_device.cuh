@@ -1,8 +1,7 @@
 // Learned proposal of technique (3) inside the path kernels: integer input
-// features of x_D, the von Mises-Fisher mixture decoded from the network's
-// outputs, its density and sampling, all in double precision so that the
-// sampled direction and the value ratio p_cos / q depend only on the exact
-// integer network outputs.
+// features of x_D (double precision, then quantised), the von Mises-Fisher
+// mixture decoded from the network's exact outputs, its density, and the
+// sampled direction (double precision).
 #pragma once
 
 #include "guide.h"
@@ -24,48 +23,67 @@ static __device__ void guide_encode_d(const float *box, double3 p, float3 n, int
         const double r = rint(128.0 * e);
         return (int8_t)(int)fmin(127.0, fmax(-127.0, r));
     };
+    // one sincospi per coordinate, then the double-angle formulas
+    // sin 2a = 2 sin a cos a, cos 2a = cos^2 a - sin^2 a: five doublings keep
+    // the error within a few 1e-15, far below the quantisation step 1/128
     for (int v = 0; v < 2; ++v)
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c) {
+            double s, co;
+            sincospi(v == 0 ? u[c] : nn[c], &s, &co);
             for (int f = 0; f < 6; ++f) {
-                const double a = ldexp(v == 0 ? u[c] : nn[c], f);
-                double s, co;
-                sincos(kPiD * a, &s, &co);
                 m[i++] = q(s);
                 m[i++] = q(co);
+                const double s2 = 2.0 * s * co, c2 = co * co - s * s;
+                s = s2;
+                co = c2;
             }
+        }
     for (int c = 0; c < 3; ++c) m[i++] = q(u[c]);
     for (int c = 0; c < 3; ++c) m[i++] = q(nn[c]);
     m[78] = 127;
     m[79] = 0;
 }
 
-struct MixD {
+// The mixture weights and concentrations in single precision (they only
+// scale values and pick a lobe); the lobe directions in double, because the
+// density exp(kappa (mu.w - 1)) multiplies the error of mu.w - 1 by kappa
+// (up to 493).
+struct MixF {
     double3 mu[kGLobes];
-    double kappa[kGLobes], pi[kGLobes];
+    float kappa[kGLobes], pi[kGLobes], norm[kGLobes];   // norm = kappa / (2 pi (1 - e^-2kappa))
 };
 
 // lobe j: outputs 5j..5j+2 direction (normalised), 5j+3 log kappa clamped to
 // [-4, 6.2], 5j+4 logit (softmax over the lobes)
-static __device__ void guide_mixture_d(const float *o, MixD &M) {
-    double mx = o[4];
-    for (int j = 1; j < kGLobes; ++j) mx = fmax(mx, (double)o[5 * j + 4]);
-    double sum = 0.0;
+static __device__ void guide_mixture_f(const float *o, MixF &M) {
+    float mx = o[4];
+#pragma unroll
+    for (int j = 1; j < kGLobes; ++j) mx = fmaxf(mx, o[5 * j + 4]);
+    float sum = 0.f;
+#pragma unroll
     for (int j = 0; j < kGLobes; ++j) {
-        M.pi[j] = exp((double)o[5 * j + 4] - mx);
+        M.pi[j] = expf(o[5 * j + 4] - mx);
         sum += M.pi[j];
     }
+    const float inv = 1.f / sum;
+#pragma unroll
     for (int j = 0; j < kGLobes; ++j) {
-        M.pi[j] /= sum;
+        M.pi[j] *= inv;
         const double3 m = d3(o[5 * j], o[5 * j + 1], o[5 * j + 2]);
         const double l = sqrt(ddot(m, m));
         M.mu[j] = l > 1e-12 ? dscale(m, 1.0 / l) : d3(0.0, 0.0, 1.0);
-        M.kappa[j] = exp(fmin(6.2, fmax(-4.0, (double)o[5 * j + 3])));
+        const float k = expf(fminf(6.2f, fmaxf(-4.0f, o[5 * j + 3])));
+        M.kappa[j] = k;
+        M.norm[j] = k / (2.f * kPi * -expm1f(-2.f * k));
     }
 }
 
-// kappa / (2 pi (1 - exp(-2 kappa))) exp(kappa (mu.w - 1))
-static __device__ __forceinline__ double vmf_pdf_d(double3 mu, double kappa, double3 w) {
-    return kappa / (2.0 * kPiD * -expm1(-2.0 * kappa)) * exp(kappa * (ddot(mu, w) - 1.0));
+static __device__ __forceinline__ float mix_pdf_f(const MixF &M, double3 w) {
+    float p = 0.f;
+#pragma unroll
+    for (int j = 0; j < kGLobes; ++j)
+        p += M.pi[j] * M.norm[j] * expf(M.kappa[j] * (float)(ddot(M.mu[j], w) - 1.0));
+    return p;
 }
 
 // inversion of the vMF cosine CDF (Jakob 2012) and a uniform azimuth in the
@@ -82,11 +100,6 @@ static __device__ double3 vmf_sample_d(const DevScene &S, double3 mu, double kap
     return dadd(dadd(dscale(t, s * cp), dscale(b, s * sp)), dscale(mu, c));
 }
 
-static __device__ double mix_pdf_d(const MixD &M, double3 w) {
-    double p = 0.0;
-    for (int j = 0; j < kGLobes; ++j) p += M.pi[j] * vmf_pdf_d(M.mu[j], M.kappa[j], w);
-    return p;
-}
 
 // transpose of the linear part of a 3x4 row-major transform times a
 static __device__ __forceinline__ double3 dlinear_T(const float *M, double3 a) {

@@ -226,28 +226,28 @@ __global__ void __launch_bounds__(256) k_start3g(const __grid_constant__ LaunchA
         const uint32_t root = A.root_begin + r;
         const Vtx xD = load_vtx(c, W, 0, r);
         const float4 u = draw(A.seed, root, T_3, g, SD_LIGHT, 1);
-        MixD mix;
-        guide_mixture_d(A.G.gout + (size_t)r * kGOut, mix);
+        MixF mix;
+        guide_mixture_f(A.G.gout + (size_t)r * kGOut, mix);
         const double3 nw = d3(xD.n);
         double3 w, wl;
         if (u.z < 0.5f) {
             w = cosine_dir_d(A.S, nw, u.x, u.y);
             wl = dlinear_T(M, w);
         } else {
-            const double v = 2.0 * (double)u.z - 1.0;
-            double acc = 0.0;
+            const float v = 2.f * u.z - 1.f;       // exact: u is on the 2^-24 grid
+            float acc = 0.f;
             int j = kGLobes - 1;
             for (int i = 0; i < kGLobes; ++i) {
                 acc += mix.pi[i];
                 if (v < acc) { j = i; break; }
             }
-            wl = vmf_sample_d(A.S, mix.mu[j], mix.kappa[j], u.x, u.y);
+            wl = vmf_sample_d(A.S, mix.mu[j], (double)mix.kappa[j], u.x, u.y);
             w = dlinear(M, wl);
         }
         const double cw = ddot(nw, w);
-        const double pc = cw > 0.0 ? cw / kPiD : 0.0;
-        const double pv = mix_pdf_d(mix, wl);
-        A.G.gratio[r] = (float)(pc / (0.5 * pc + 0.5 * pv));
+        const float pc = cw > 0.0 ? (float)(cw / kPiD) : 0.f;
+        const float pv = mix_pdf_f(mix, wl);
+        A.G.gratio[r] = pc / (0.5f * pc + 0.5f * pv);
         const uint32_t slot = guide_slot(A.G, g, root);
         if (slot != ~0u) {
             const uint32_t C = A.G.smp.cap;

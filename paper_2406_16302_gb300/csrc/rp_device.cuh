@@ -707,18 +707,21 @@ static __device__ __forceinline__ int camera_project(const DevScene &S, float3 p
 // path contribution (Eq. pathcontribution, pinhole importance), no visibility
 // ---------------------------------------------------------------------------
 
-static __device__ float3 path_throughput(const Ctx &c, int g, const Vtx *x, int k, int &pix) {
+// the factors are single precision; their product is accumulated in double
+// so that walks through near-coincident vertices (geometric terms of 1e8 and
+// more per edge) cannot overflow
+static __device__ double3 path_throughput(const Ctx &c, int g, const Vtx *x, int k, int &pix) {
     const DevScene &S = c.A.S;
     float cc;
     pix = camera_project(S, x[1].p, cc);
-    if (pix < 0) return f3(0, 0, 0);
+    if (pix < 0) return d3(0.0, 0.0, 0.0);
     float3 d01 = x[0].p - x[1].p;
     float r2 = dot3(d01, d01);
     float c1 = dot3(x[1].n, d01) / sqrtf(r2);
-    if (c1 <= 0.f) return f3(0, 0, 0);
+    if (c1 <= 0.f) return d3(0.0, 0.0, 0.0);
     float We = 1.0f / (S.pix_area * cc * cc * cc);
-    float s0 = We * c1 / r2;
-    float3 f = f3(s0, s0, s0);
+    double s0 = (double)(We * c1) / (double)r2;
+    double3 f = d3(s0, s0, s0);
     for (int j = 1; j <= k - 2; ++j) {
         float3 wi = unit3(x[j - 1].p - x[j].p);
         float3 e = x[j + 1].p - x[j].p;
@@ -726,13 +729,20 @@ static __device__ float3 path_throughput(const Ctx &c, int g, const Vtx *x, int 
         float3 wo = e * (1.0f / sqrtf(r2e));
         Mat m = get_mat(c, g, x[j].mat);
         float3 rho = bsdf_eval(m, x[j].n, wi, wo);
-        if (zero3(rho)) return f3(0, 0, 0);
+        if (zero3(rho)) return d3(0.0, 0.0, 0.0);
         float ca = dot3(x[j].n, wo), cb = -dot3(x[j + 1].n, wo);
-        if (ca <= 0.f || cb <= 0.f) return f3(0, 0, 0);
-        f = mul3(f, rho) * (ca * cb / r2e);
+        if (ca <= 0.f || cb <= 0.f) return d3(0.0, 0.0, 0.0);
+        const double gt = (double)(ca * cb) / (double)r2e;
+        f = d3(f.x * rho.x * gt, f.y * rho.y * gt, f.z * rho.z * gt);
     }
     Mat em = get_mat(c, g, x[k - 1].mat);
-    return mul3(f, em.em);
+    return d3(f.x * em.em.x, f.y * em.em.y, f.z * em.em.z);
+}
+
+static __device__ __forceinline__ bool zero3d(double3 a) { return a.x == 0.0 && a.y == 0.0 && a.z == 0.0; }
+
+static __device__ __forceinline__ float3 scale3d(double3 a, double s) {
+    return f3((float)(a.x * s), (float)(a.y * s), (float)(a.z * s));
 }
 
 // ---------------------------------------------------------------------------
@@ -765,19 +775,21 @@ static __device__ float step_pdf(const Ctx &c, int g, const Vtx *x, int cond, in
     return area_from_dir(bsdf_pdf(m, x[at].n, wc, wo), x[at].p, x[to]);
 }
 
-static __device__ float mis_denominator(const Ctx &c, int g, const Vtx *x, int k) {
+// per-technique densities are products of single-precision factors
+// accumulated in double (see path_throughput)
+static __device__ double mis_denominator(const Ctx &c, int g, const Vtx *x, int k) {
     const DevScene &S = c.A.S;
     const int tm = c.A.tech_mask;
     const bool t1 = tm & 1, t2 = tm & 2, t3 = tm & 4, t7 = tm & 8;
-    if (k == 2) return t7 ? pdf_camera_area(S, x[1]) : 0.f;
+    if (k == 2) return t7 ? pdf_camera_area(S, x[1]) : 0.0;
     float pE[kMaxVerts], pL[kMaxVerts];
-    const float pD = 1.0f / S.dyn_area, pLi = 1.0f / S.emit_area;
+    const double pD = 1.0 / S.dyn_area, pLi = 1.0 / S.emit_area;
     pE[1] = pdf_camera_area(S, x[1]);
     for (int j = 2; j <= k - 2; ++j) pE[j] = step_pdf(c, g, x, j - 2, j - 1, j);
     for (int j = 1; j <= k - 3; ++j) pL[j] = step_pdf(c, g, x, j + 2, j + 1, j);
-    float sum = 0.f;
+    double sum = 0.0;
     if (t7) {
-        float p = pLi;
+        double p = pLi;
         for (int j = 1; j <= k - 2; ++j) p *= pE[j];
         sum += p;
     }
@@ -785,18 +797,18 @@ static __device__ float mis_denominator(const Ctx &c, int g, const Vtx *x, int k
         if (!is_dyn(c, x[i])) continue;
         if (i == k - 2) {                    // (1) dynamic from emitter
             if (!t1) continue;
-            float p = pD * pLi;
+            double p = pD * pLi;
             for (int j = 1; j <= k - 3; ++j) p *= pL[j];
             sum += p;
         } else if (i == 1) {                 // (2) dynamic from sensor
             if (!t2) continue;
-            float p = pD * pLi;
+            double p = pD * pLi;
             for (int j = 2; j <= k - 2; ++j) p *= pE[j];
             sum += p;
         } else {                             // (3) dynamic two ends
             if (!t3) continue;
             float3 w = unit3(x[i + 1].p - x[i].p);
-            float p = pD * pLi * area_from_dir(cosine_pdf(x[i].n, w), x[i].p, x[i + 1]);
+            double p = pD * pLi * area_from_dir(cosine_pdf(x[i].n, w), x[i].p, x[i + 1]);
             for (int j = i + 2; j <= k - 2; ++j) p *= pE[j];
             for (int j = 1; j <= i - 1; ++j) p *= pL[j];
             sum += p;
@@ -1033,29 +1045,29 @@ struct PathCounts {
 static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x, int n, uint32_t root,
                               int tech, int sa, int sb, bool residual, bool static_known = false) {
     int pa;
-    float3 fx = path_throughput(c, g, x, n, pa);
-    if (zero3(fx)) return;
-    const float invN = c.A.invN;
+    const double3 fx = path_throughput(c, g, x, n, pa);
+    if (zero3d(fx)) return;
+    const double invN = c.A.invN;
     if (!residual) {               // primal path tracing: one technique
-        float p = 0.f;
+        double p = 0.0;
         {
             // path tracing density alone
             const DevScene &S = c.A.S;
             if (n == 2) {
                 p = pdf_camera_area(S, x[1]);
             } else {
-                p = pdf_camera_area(S, x[1]) / S.emit_area;
+                p = (double)pdf_camera_area(S, x[1]) / S.emit_area;
                 for (int j = 2; j <= n - 2; ++j) p *= step_pdf(c, g, x, j - 2, j - 1, j);
             }
         }
         ++pc.paths;
-        emit(c, root, tech, g, sa, sb, pa, fx * (invN / p), -1, f3(0, 0, 0), 0, p, 0.f, 1.f);
+        emit(c, root, tech, g, sa, sb, pa, scale3d(fx, invN / p), -1, f3(0, 0, 0), 0, (float)p, 0.f, 1.f);
         return;
     }
     if (tech == T_7 && !static_known && path_is_static(c, g, x, n)) return;
     ++pc.paths;
-    const float Pg = mis_denominator(c, g, x, n);
-    const float sign = (g == 2) ? 1.0f : -1.0f;
+    const double Pg = mis_denominator(c, g, x, n);
+    const double sign = (g == 2) ? 1.0 : -1.0;
     const int g2 = 3 - g;
     Vtx y[kMaxVerts];
     MapInfo mi;
@@ -1067,31 +1079,31 @@ static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x
     } else {
         map_path(c, g, g2, x, n, y, mi);
     }
-    float3 fy = f3(0, 0, 0);
+    double3 fy = d3(0.0, 0.0, 0.0);
     int pb = -1;
-    float Py = 0.f;
+    double Py = 0.0;
     if (mi.status == MAP_ACCEPT) {
         if (c.A.E.motion && !mapped_visible(c, g2, x, y, n, mi)) {
             mi.status = MAP_INVALID;
         } else {
             fy = path_throughput(c, g2, y, n, pb);
-            if (zero3(fy)) {
+            if (zero3d(fy)) {
                 mi.status = MAP_INVALID;
             } else {
                 Py = mis_denominator(c, g2, y, n);
-                if (!(Py > 0.f)) mi.status = MAP_INVALID;
+                if (!(Py > 0.0)) mi.status = MAP_INVALID;
             }
         }
     }
     if (mi.status == MAP_ACCEPT) {
         ++pc.accepted;
-        float den = (Pg + Py * mi.J) / invN;
-        emit(c, root, tech, g, sa, sb, pa, fx * (sign / den), pb, fy * (-sign * mi.J / den),
-             mi.status, Pg, Py, mi.J);
+        const double den = (Pg + Py * mi.J) / invN;
+        emit(c, root, tech, g, sa, sb, pa, scale3d(fx, sign / den), pb, scale3d(fy, -sign * mi.J / den),
+             mi.status, (float)Pg, (float)Py, mi.J);
     } else {
         if (mi.status != MAP_INVALID) ++pc.rejected;
-        emit(c, root, tech, g, sa, sb, pa, fx * (sign * invN / Pg), -1, f3(0, 0, 0), mi.status,
-             Pg, 0.f, 0.f);
+        emit(c, root, tech, g, sa, sb, pa, scale3d(fx, sign * invN / Pg), -1, f3(0, 0, 0), mi.status,
+             (float)Pg, 0.f, 0.f);
     }
 }
 
