@@ -86,6 +86,14 @@ typedef struct {
     /* reconnection thresholds alpha_min and d_min and the Jacobian threshold
      * (Sec. 5, "Keep vertex the same" criteria 2 and 3, "Path rejection") */
     float alpha_min, d_min, jacobian_max;
+    /* further movable objects (may be 0 / NULL): object k (k = 1 .. n_objects)
+     * is the range object_ranges[2(k-1)] (first static triangle) ..
+     * + object_ranges[2(k-1)+1] (count) of the static triangles; it stays
+     * static unless an edit moves it, and its given coordinates are its
+     * object space (an edit's M1, M2 map them to each frame).  Movable
+     * objects may not be emissive. */
+    uint32_t n_objects;
+    const uint32_t *object_ranges;
 } rp_scene_desc;
 
 typedef struct rp_scene_s rp_scene;
@@ -110,6 +118,10 @@ void rp_scene_destroy(rp_scene *scene);
 typedef struct {
     float M1[12], M2[12];
     float mat1[RP_MATERIAL_FLOATS], mat2[RP_MATERIAL_FLOATS];
+    /* the edited object: 0 = the dynamic mesh of the scene description,
+     * k >= 1 = movable object k (its base pose in the static geometry is
+     * replaced by the object under M1 / M2) */
+    uint32_t object;
 } rp_edit_desc;
 
 rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out);
@@ -311,6 +323,52 @@ rp_status rp_guide_status(rp_guide *guide);
  * one-thread-per-root entry point (rp_render_residual_f32_noalloc) never
  * uses it. */
 rp_status rp_scene_set_guide(rp_scene *scene, rp_guide *guide);
+
+/* ------------------------------------------------------------------------
+ * Batches of edits (animation frames) of one scene, each with its own image
+ * size, sample count, seed and output, run as one CUDA graph: every wave of
+ * every item is captured once; items are spread over `streams` concurrent
+ * branches (longest first to the least loaded), each with its own
+ * wavefront buffers, so that the tail of one item's waves overlaps another
+ * item's.  Not in the paper (which names rendering many frames as future
+ * work); each item's result equals rp_render_residual of that item. */
+typedef struct {
+    const rp_edit_handle *edit;  /* an edit of the batch's scene */
+    uint32_t width, height;      /* image size; 0, 0: the scene's */
+    uint32_t spp;
+    uint64_t seed;               /* replaced by rp_batch_set_seeds */
+    uint32_t tech_mask;
+    double *d_out;               /* [height][width][3] device image, accumulated into; caller-owned,
+                                    valid for the batch's lifetime */
+} rp_batch_item;
+
+typedef struct {
+    uint32_t wave_roots;         /* roots per wave (0: min(largest item, 2^22)) */
+    uint32_t streams;            /* concurrent branches, 1..8 (0: 1) */
+    uint32_t blocks_per_sm;      /* grid of the queue kernels per SM, 1..64 (0: 16) */
+} rp_batch_config;
+
+typedef struct rp_batch_s rp_batch;
+
+/* Capture the batch (allocates the branches' wavefront buffers; config NULL:
+ * defaults).  The edits must outlive the batch; the scene's guide is not
+ * used.  Synchronous.  Errors: RP_ERR_INVALID_ARG, RP_ERR_OOM, RP_ERR_CUDA. */
+rp_status rp_batch_create(rp_scene *scene, const rp_batch_item *items, uint32_t n,
+                          const rp_batch_config *config, rp_batch **out);
+void rp_batch_destroy(rp_batch *batch);
+/* One graph launch on `stream`: every item's residual added to its image. */
+rp_status rp_batch_launch(rp_batch *batch, void *stream);
+/* Stream-ordered upload of new per-item seeds (n values) for later launches. */
+rp_status rp_batch_set_seeds(rp_batch *batch, const uint64_t *seeds, void *stream);
+/* The configuration in use and the number of graph nodes. */
+rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *graph_nodes);
+/* Autotuner: times candidate configurations on a proxy of the batch (each
+ * item's spp divided by spp_divisor, outputs into a scratch image) by
+ * coordinate descent over wave_roots (2^20 .. 2^23), streams (1, 2, 4) and
+ * blocks_per_sm (8, 16, 32) from the defaults; writes the fastest and its
+ * proxy time in ms.  Synchronous; leaves the items' images untouched. */
+rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *items, uint32_t n,
+                            uint32_t spp_divisor, rp_batch_config *best, double *best_ms);
 
 /* Thread-local message describing the last error (empty string if none). */
 const char *rp_last_error(void);

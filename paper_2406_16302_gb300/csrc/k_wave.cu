@@ -99,7 +99,7 @@ __device__ __forceinline__ void continue_walk(const Ctx &c, int buf, int it, uin
                                               const Vtx &prev, const Vtx &at, int tech, int rg,
                                               int side, int step) {
     const LaunchArgs &A = c.A;
-    float4 u = draw(A.seed, A.root_begin + r, tech, rg, side, step);
+    float4 u = draw(lseed(A), A.root_begin + r, tech, rg, side, step);
     float3 wc = unit3(prev.p - at.p);
     float3 wo;
     Mat m = get_mat(c, A.frame, at.mat);
@@ -127,10 +127,10 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
         W.ghost_w[r] = 0u;
         W.ghost_n[r] = 0u;
         if (T == T_1 || T == T_2 || T == T_3) {
-            Vtx xD = sample_dynamic(c, g, draw(A.seed, root, T, g, SD_ROOT, 0));
+            Vtx xD = sample_dynamic(c, g, draw(lseed(A), root, T, g, SD_ROOT, 0));
             store_vtx(W, 0, r, xD);
             if (T == T_1) {
-                Vtx xL = sample_emitter(c, g, draw(A.seed, root, T_1, g, SD_NEE, 0));
+                Vtx xL = sample_emitter(c, g, draw(lseed(A), root, T_1, g, SD_NEE, 0));
                 store_vtx(W, 1, r, xL);
                 if (faces(xD, xL.p) && faces(xL, xD.p)) push_shadow(A, 0, xD, xL, make_tag(r, CK_NEE, 0));
             } else if (T == T_2) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                 if (A.G.on) {
                     // learned proposal: object-space x_D and normal for the
                     // network's input and the training samples
-                    const float4 ur = draw(A.seed, root, T_3, g, SD_ROOT, 0);
+                    const float4 ur = draw(lseed(A), root, T_3, g, SD_ROOT, 0);
                     const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
                     double b1, b2;
                     tri_sample(ur.y, ur.z, b1, b2);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                     }
                 }
                 if (live) {
-                    float4 u = draw(A.seed, root, T_3, g, SD_LIGHT, 1);
+                    float4 u = draw(lseed(A), root, T_3, g, SD_LIGHT, 1);
                     float3 w = cosine_dir_walk(A.S, xD.n, u.x, u.y);
                     if (A.G.on) {
                         const uint32_t slot = guide_slot(A.G, g, root);
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
             const int rg = A.residual ? g : 0;
             const uint32_t npix = (uint32_t)(A.S.W * A.S.H);
             const int pix = (int)(root % npix);
-            float4 u = draw(A.seed, root, tech, rg, SD_ROOT, 0);
+            float4 u = draw(lseed(A), root, tech, rg, SD_ROOT, 0);
             float3 d = camera_dir(A.S, pix % A.S.W, pix / A.S.W, u.x, u.y);
             push_closest(A, 0, 0, A.S.cam_pos, d, -1, make_tag(r, SIDE_ROOT, 0));
         }
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(128) k_encode3(const __grid_constant__ LaunchA
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         if (!(A.W.flags[r] & RF_GUIDE)) continue;
         const uint32_t root = A.root_begin + r;
-        const float4 ur = draw(A.seed, root, T_3, g, SD_ROOT, 0);
+        const float4 ur = draw(lseed(A), root, T_3, g, SD_ROOT, 0);
         const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
         double b1, b2;
         tri_sample(ur.y, ur.z, b1, b2);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_start3g(const __grid_constant__ LaunchA
         if (!(W.flags[r] & RF_GUIDE)) continue;
         const uint32_t root = A.root_begin + r;
         const Vtx xD = load_vtx(c, W, 0, r);
-        const float4 u = draw(A.seed, root, T_3, g, SD_LIGHT, 1);
+        const float4 u = draw(lseed(A), root, T_3, g, SD_LIGHT, 1);
         MixF mix;
         guide_mixture_f(A.G.gout + (size_t)r * kGOut, mix);
         const double3 nw = d3(xD.n);
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
             Vtx prev = (j == 1) ? camera_vertex(c) : load_vtx(c, W, j == 2 ? 0 : slot_light(D, j - 2), r);
             if (ghosts) push_shadow(A, it + 1, prev, v, make_tag(r, CK_GHOST_WALK, j));
             if (vtx_black(c, g, v)) continue;
-            Vtx L = sample_emitter(c, g, draw(A.seed, root, tech, rg, SD_NEE, j));
+            Vtx L = sample_emitter(c, g, draw(lseed(A), root, tech, rg, SD_NEE, j));
             store_vtx(W, slot_nee(D, j), r, L);
             if (faces(v, L.p) && faces(L, v.p)) {
                 push_shadow(A, it + 1, v, L, make_tag(r, CK_NEE, j));
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
             // techniques (2) and (3): light-side walk vertex y_m with next-event estimation
             store_vtx(W, slot_light(D, m), r, v);
             W.len_light[r] = m;
-            Vtx L = sample_emitter(c, g, draw(A.seed, root, T, g, SD_NEE, m));
+            Vtx L = sample_emitter(c, g, draw(lseed(A), root, T, g, SD_NEE, m));
             store_vtx(W, slot_nee(D, m), r, L);
             if (faces(v, L.p) && faces(L, v.p)) push_shadow(A, it + 1, v, L, make_tag(r, CK_NEE, m));
             const int last = (T == T_2) ? D - 2 : D - 3;
@@ -661,7 +661,7 @@ cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
     const uint32_t n = a.root_end - a.root_begin;
     const int D = a.S.max_depth;
     const int gR = grid_for(n, 256, 1 << 20);
-    const int gQ = 152 * 16;                 // persistent-style grids over device-side counts
+    const int gQ = a.grid_q > 0 ? a.grid_q : 152 * 16;   // persistent-style grids over device-side counts
     cudaError_t e = cudaMemsetAsync(a.W.counts, 0, sizeof(unsigned int) * kCountSlots, s);
     if (e != cudaSuccess) return e;
     RP_LAUNCH("k_gen", gR, 256, k_gen<T>, a);

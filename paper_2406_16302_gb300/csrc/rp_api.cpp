@@ -86,6 +86,8 @@ struct rp_guide_s {
 
 struct rp_scene_s {
     DevScene S{};
+    std::vector<DevObject> objects;   // 0: the dynamic mesh; k >= 1: static triangle ranges
+    double cam_hh = 0.0;              // tan(vfov / 2)
     std::vector<void *> allocs;
     int bvh_depth_static = 0, bvh_depth_dyn = 0;
     unsigned long long *d_stats = nullptr;
@@ -171,6 +173,17 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
     for (uint32_t i = 0; i < d->n_materials; ++i)
         if (!material_ok(d->materials + 12 * i))
             return fail(RP_ERR_INVALID_ARG, "invalid material row");
+    if (d->n_objects && !d->object_ranges) return fail(RP_ERR_INVALID_ARG, "null object_ranges");
+    for (uint32_t k = 0; k < d->n_objects; ++k) {
+        const uint64_t first = d->object_ranges[2 * k], count = d->object_ranges[2 * k + 1];
+        if (count == 0 || first + count > d->n_static_triangles)
+            return fail(RP_ERR_INVALID_ARG, "object range outside the static triangles");
+        for (uint64_t i = first; i < first + count; ++i) {
+            const float *m = d->materials + 12 * d->static_material[i];
+            if (m[8] != 0.f || m[9] != 0.f || m[10] != 0.f)
+                return fail(RP_ERR_UNSUPPORTED, "a movable object may not be emissive");
+        }
+    }
 
     const int ns = (int)d->n_static_triangles, nd = (int)d->n_dyn_triangles;
     rp_scene *sc = new rp_scene_s();
@@ -288,6 +301,56 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
     S.n_mats = (int)d->n_materials;
     S.dyn_area = (float)dyn_area;
     S.emit_area = (float)acc;
+    {
+        DevObject o0{};
+        o0.bvh = S.dyn;
+        o0.tri = S.dyn_tri;
+        o0.cdf = S.dyn_cdf;
+        o0.n = nd;
+        o0.area = S.dyn_area;
+        sc->objects.push_back(o0);
+    }
+    // movable objects: a BVH in object space (their given coordinates), the
+    // triangles by id and the area sampling table, as for the dynamic mesh
+    for (uint32_t k = 0; k < d->n_objects; ++k) {
+        const int first = (int)d->object_ranges[2 * k], count = (int)d->object_ranges[2 * k + 1];
+        const uint32_t *tri = d->static_triangles + 3 * (size_t)first;
+        BuiltBVH bo = build_bvh(d->static_vertices, tri, count, ns);
+        if (bo.depth >= kStackDepth) {
+            delete sc;
+            return fail(RP_ERR_UNSUPPORTED, "BVH deeper than the traversal stack");
+        }
+        std::vector<float4> ot(3 * (size_t)count);
+        for (int i = 0; i < count; ++i) fill(d->static_vertices, tri + 3 * i, &ot[3 * (size_t)i]);
+        std::vector<double> oacc(count);
+        double oa = 0.0;
+        for (int i = 0; i < count; ++i) { oa += area(&ot[3 * (size_t)i]); oacc[i] = oa; }
+        if (!(oa > 0.0)) {
+            delete sc;
+            return fail(RP_ERR_INVALID_ARG, "movable object of zero area");
+        }
+        std::vector<uint32_t> ocdf(count);
+        for (int i = 0; i < count; ++i) ocdf[i] = threshold(oacc[i] / oa);
+        ocdf[count - 1] = 16777216u;
+        DevObject o{};
+        float4 *q4;
+        uint32_t *qu;
+        if ((s = upload(bo.nodes, &q4)) != RP_OK) { delete sc; return s; }
+        keep(q4); o.bvh.nodes = q4;
+        if ((s = upload(bo.tris, &q4)) != RP_OK) { delete sc; return s; }
+        keep(q4); o.bvh.tris = q4;
+        if ((s = upload(ot, &q4)) != RP_OK) { delete sc; return s; }
+        keep(q4); o.tri = q4;
+        if ((s = upload(ocdf, &qu)) != RP_OK) { delete sc; return s; }
+        keep(qu); o.cdf = qu;
+        o.bvh.n_nodes = (int)(bo.nodes.size() / 4);
+        o.bvh.n_tris = count;
+        o.n = count;
+        o.area = (float)oa;
+        o.skip_lo = first;
+        o.skip_n = count;
+        sc->objects.push_back(o);
+    }
     // camera basis in double, stored as float
     const float *c = d->camera;
     double pos[3] = {c[0], c[1], c[2]}, look[3] = {c[3], c[4], c[5]}, up[3] = {c[6], c[7], c[8]};
@@ -307,6 +370,7 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
     S.cam_right = make_float3((float)r[0], (float)r[1], (float)r[2]);
     S.cam_up = make_float3((float)u[0], (float)u[1], (float)u[2]);
     double hh = std::tan(0.5 * (double)c[9] * 3.14159265358979323846 / 180.0);
+    sc->cam_hh = hh;
     double hw = hh * d->width / d->height;
     S.hh = (float)hh;
     S.hw = (float)hw;
@@ -363,7 +427,9 @@ static bool rigid(const float *M) {
     return det > 0.0;
 }
 
-static rp_status fill_edit(const rp_edit_desc *d, DevEdit &E) {
+static rp_status fill_edit(const rp_scene *sc, const rp_edit_desc *d, DevEdit &E) {
+    if (d->object >= sc->objects.size())
+        return fail(RP_ERR_INVALID_ARG, "edit object index out of range");
     if (!rigid(d->M1) || !rigid(d->M2))
         return fail(RP_ERR_UNSUPPORTED, "edit transforms must be rigid (rotation + translation)");
     if (!material_ok(d->mat1) || !material_ok(d->mat2))
@@ -379,14 +445,41 @@ static rp_status fill_edit(const rp_edit_desc *d, DevEdit &E) {
     std::memcpy(E.mat[1], d->mat1, sizeof(float) * 12);
     std::memcpy(E.mat[2], d->mat2, sizeof(float) * 12);
     E.motion = std::memcmp(d->M1, d->M2, sizeof(float) * 12) != 0;
+    E.object = (int)d->object;
+    E.skip_lo = sc->objects[d->object].skip_lo;
+    E.skip_n = sc->objects[d->object].skip_n;
     return RP_OK;
+}
+
+// the scene as seen by an edit: its moved object in the dynamic slots
+static DevScene scene_for_edit(const rp_scene *sc, const DevEdit &E) {
+    DevScene S = sc->S;
+    const DevObject &o = sc->objects[E.object];
+    S.dyn = o.bvh;
+    S.dyn_tri = o.tri;
+    S.dyn_cdf = o.cdf;
+    S.n_dyn = o.n;
+    S.dyn_area = o.area;
+    return S;
+}
+
+// the camera for an image of W x H pixels (same position, basis and
+// vertical field of view)
+static void set_resolution(const rp_scene *sc, DevScene &S, int W, int H) {
+    const double hh = sc->cam_hh, hw = hh * W / H;
+    S.hh = (float)hh;
+    S.hw = (float)hw;
+    S.pix_area = (float)((2.0 * hw / W) * (2.0 * hh / H));
+    S.film_area = (float)(4.0 * hw * hh);
+    S.W = W;
+    S.H = H;
 }
 
 extern "C" rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out) {
     if (!scene || !desc || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     rp_edit_handle *e = new rp_edit_s();
-    rp_status s = fill_edit(desc, e->E);
+    rp_status s = fill_edit(scene, desc, e->E);
     if (s != RP_OK) {
         delete e;
         return s;
@@ -400,7 +493,7 @@ extern "C" void rp_edit_destroy(rp_edit_handle *edit) { delete edit; }
 static LaunchArgs base_args(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
                             uint32_t mask) {
     LaunchArgs a{};
-    a.S = sc->S;
+    a.S = scene_for_edit(sc, E);
     a.E = E;
     a.seed = seed;
     a.invN = (float)(1.0 / ((double)spp * sc->S.W * sc->S.H));
@@ -452,13 +545,10 @@ static rp_status ensure_guide_buffers(rp_scene *sc) {
     return RP_OK;
 }
 
-static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
-    const int D = sc->S.max_depth;
-    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return ensure_guide_buffers(sc);
-    R = std::max(R, sc->W.R);
-    tasks = tasks || sc->wave_tasks;
-    sc->free_wave();
-    WaveBuf &W = sc->W;
+// wavefront buffers for waves of up to R roots of paths with at most D
+// edges; `tasks` adds the mapping task queue needed by edits with motion
+static rp_status alloc_wavebuf(WaveBuf &W, std::vector<void *> &allocs, uint32_t R, int D, bool tasks) {
+    W = WaveBuf{};
     W.R = R;
     W.S = slot_count(D);
     W.qc = 2 * R;
@@ -467,15 +557,20 @@ static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
     W.qt = tasks ? (uint32_t)std::min<uint64_t>((uint64_t)R * (uint64_t)std::max(D + 1, t3),
                                                  0xffffffffull)
                  : 0u;
+    auto free_all = [&]() {
+        for (void *p : allocs) cudaFree(p);
+        allocs.clear();
+        W = WaveBuf{};
+    };
     auto alloc = [&](void **p, size_t bytes) -> rp_status {
         cudaError_t e = cudaMalloc(p, bytes);
         if (e == cudaErrorMemoryAllocation) return fail(RP_ERR_OOM, "wavefront buffer allocation failed");
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc wavefront");
-        sc->wave_allocs.push_back(*p);
+        allocs.push_back(*p);
         return RP_OK;
     };
     const size_t SR = (size_t)W.S * R;
-#define A_(ptr, bytes) if (rp_status s_ = alloc((void **)&(ptr), (bytes))) { sc->free_wave(); return s_; }
+#define A_(ptr, bytes) if (rp_status s_ = alloc((void **)&(ptr), (bytes))) { free_all(); return s_; }
     A_(W.px, SR * 4) A_(W.py, SR * 4) A_(W.pz, SR * 4) A_(W.nx, SR * 4) A_(W.ny, SR * 4)
     A_(W.nz, SR * 4) A_(W.b1, SR * 4) A_(W.b2, SR * 4) A_(W.prim, SR * 4)
     A_(W.len_eye, R * 4ull) A_(W.len_light, R * 4ull) A_(W.flags, R * 4ull)
@@ -491,6 +586,16 @@ static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
     if (tasks) { A_(W.tasks, W.qt * 16ull) }
     A_(W.counts, kCountSlots * 4ull)
 #undef A_
+    return RP_OK;
+}
+
+static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
+    const int D = sc->S.max_depth;
+    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return ensure_guide_buffers(sc);
+    R = std::max(R, sc->W.R);
+    tasks = tasks || sc->wave_tasks;
+    sc->free_wave();
+    if (rp_status s = alloc_wavebuf(sc->W, sc->wave_allocs, R, D, tasks)) return s;
     sc->wave_tasks = tasks;
     return ensure_guide_buffers(sc);
 }
@@ -596,7 +701,7 @@ extern "C" rp_status rp_render_residual_host(rp_scene *scene, const rp_edit_desc
     if (rp_status s = check_render(scene, spp, tech_mask)) return s;
     if (!edit || !host_out) return fail(RP_ERR_INVALID_ARG, "null edit or image");
     DevEdit E;
-    if (rp_status s = fill_edit(edit, E)) return s;
+    if (rp_status s = fill_edit(scene, edit, E)) return s;
     if (rp_status s = ensure_scratch(scene)) return s;
     cudaStream_t st = (cudaStream_t)stream;
     size_t n = (size_t)scene->S.W * scene->S.H * 3;
@@ -659,7 +764,7 @@ extern "C" rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edi
     if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
     if (n && (!d_origins || !d_dirs || !d_t || !d_prim || !d_b1 || !d_b2))
         return fail(RP_ERR_INVALID_ARG, "null ray buffer");
-    RP_CUDA(launch_trace(scene->S, edit->E, frame, n, d_origins, d_dirs, d_t, d_prim, d_b1, d_b2,
+    RP_CUDA(launch_trace(scene_for_edit(scene, edit->E), edit->E, frame, n, d_origins, d_dirs, d_t, d_prim, d_b1, d_b2,
                          (cudaStream_t)stream),
             "trace launch");
     return RP_OK;
@@ -1029,5 +1134,296 @@ extern "C" rp_status rp_scene_set_guide(rp_scene *scene, rp_guide *guide) {
     if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
     scene->guide = guide;
     if (!guide) scene->free_guide_buffers();
+    return RP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches of edits: every wave of every item captured in one CUDA graph
+// ---------------------------------------------------------------------------
+
+struct rp_batch_s {
+    struct Item {
+        DevEdit E;
+        int W, H;
+        uint32_t spp, mask;
+        double *out;
+        uint64_t cost;
+        int branch;
+    };
+    struct Branch {
+        WaveBuf W{};
+        std::vector<void *> allocs;
+        cudaStream_t s = nullptr;
+        cudaEvent_t join = nullptr;
+    };
+    rp_scene *sc = nullptr;
+    std::vector<Item> items;
+    rp_batch_config cfg{};
+    unsigned long long *d_seeds = nullptr;
+    std::vector<Branch> br;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+    ~rp_batch_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (fork) cudaEventDestroy(fork);
+        for (Branch &b : br) {
+            for (void *p : b.allocs) cudaFree(p);
+            if (b.s) cudaStreamDestroy(b.s);
+            if (b.join) cudaEventDestroy(b.join);
+        }
+        if (d_seeds) cudaFree(d_seeds);
+    }
+};
+
+namespace {
+
+int device_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+}
+
+int popcount4(uint32_t m) { return (int)(m & 1) + (int)((m >> 1) & 1) + (int)((m >> 2) & 1) + (int)((m >> 3) & 1); }
+
+rp_status check_items(rp_scene *sc, const rp_batch_item *items, uint32_t n) {
+    if (!sc || !items || n == 0) return fail(RP_ERR_INVALID_ARG, "null scene, null items or no items");
+    for (uint32_t i = 0; i < n; ++i) {
+        const rp_batch_item &it = items[i];
+        if (!it.edit || !it.d_out) return fail(RP_ERR_INVALID_ARG, "batch item without edit or output");
+        const uint64_t W = it.width ? it.width : (uint32_t)sc->S.W, H = it.height ? it.height : (uint32_t)sc->S.H;
+        if (W == 0 || H == 0 || W * H > (1u << 26)) return fail(RP_ERR_INVALID_ARG, "item image size out of range");
+        if (it.spp == 0 || (uint64_t)it.spp * W * H > 0xffffffffull)
+            return fail(RP_ERR_INVALID_ARG, "item spp must be positive and spp * width * height fit in 32 bits");
+        if (it.tech_mask == 0 || (it.tech_mask & ~RP_TECH_ALL)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
+    }
+    return RP_OK;
+}
+
+rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, const rp_batch_config *cfg_in,
+                      rp_batch **out) {
+    if (rp_status s = check_items(sc, items, n)) return s;
+    rp_batch *b = new rp_batch_s();
+    b->sc = sc;
+    uint64_t max_roots = 1;
+    bool motion = false;
+    for (uint32_t i = 0; i < n; ++i) {
+        rp_batch_s::Item it{};
+        it.E = items[i].edit->E;
+        it.W = items[i].width ? (int)items[i].width : sc->S.W;
+        it.H = items[i].height ? (int)items[i].height : sc->S.H;
+        it.spp = items[i].spp;
+        it.mask = items[i].tech_mask;
+        it.out = items[i].d_out;
+        const uint64_t roots = (uint64_t)it.spp * it.W * it.H;
+        it.cost = roots * (uint64_t)popcount4(it.mask) * (it.E.motion ? 2 : 1);
+        max_roots = std::max(max_roots, roots);
+        motion = motion || it.E.motion;
+        b->items.push_back(it);
+    }
+    rp_batch_config c = cfg_in ? *cfg_in : rp_batch_config{};
+    if (c.wave_roots == 0) c.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, sc->wave_cap);
+    if (c.wave_roots > (1u << 24)) c.wave_roots = 1u << 24;
+    c.wave_roots = std::max<uint32_t>(c.wave_roots, 256u);
+    if (c.streams == 0) c.streams = 1;
+    c.streams = std::min<uint32_t>(c.streams, std::min<uint32_t>(8u, n));
+    if (c.blocks_per_sm == 0) c.blocks_per_sm = 16;
+    c.blocks_per_sm = std::min<uint32_t>(std::max<uint32_t>(c.blocks_per_sm, 1u), 64u);
+    b->cfg = c;
+    auto bail = [&](rp_status s) { delete b; return s; };
+    cudaError_t e = cudaMalloc((void **)&b->d_seeds, sizeof(unsigned long long) * n);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc seeds"));
+    std::vector<unsigned long long> seeds(n);
+    for (uint32_t i = 0; i < n; ++i) seeds[i] = items[i].seed;
+    e = cudaMemcpy(b->d_seeds, seeds.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "upload seeds"));
+    // longest items first, each to the least loaded branch
+    b->br.resize(c.streams);
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return b->items[x].cost > b->items[y].cost; });
+    std::vector<uint64_t> load(c.streams, 0);
+    for (uint32_t i : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->items[i].branch = k;
+        load[k] += b->items[i].cost;
+    }
+    for (rp_batch_s::Branch &br : b->br) {
+        if (rp_status s = alloc_wavebuf(br.W, br.allocs, c.wave_roots, sc->S.max_depth, motion)) return bail(s);
+        if (cudaStreamCreateWithFlags(&br.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&br.join, cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(RP_ERR_CUDA, "stream creation failed"));
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(RP_ERR_CUDA, "event creation failed"));
+    // capture: fork to the branches, every wave of every item, join
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(RP_ERR_CUDA, "stream creation failed"));
+    rp_status st = RP_OK;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, cs);
+    for (rp_batch_s::Branch &br : b->br)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(br.s, b->fork, 0);
+    const int techs[4] = {1, 2, 3, 7};
+    const int grid_q = (int)c.blocks_per_sm * device_sms();
+    for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        const rp_batch_s::Item &it = b->items[i];
+        rp_batch_s::Branch &br = b->br[it.branch];
+        LaunchArgs a = base_args(sc, it.E, it.spp, items[i].seed, it.mask);
+        a.G = GuideLaunch{};
+        a.stats = nullptr;
+        a.timer = nullptr;
+        set_resolution(sc, a.S, it.W, it.H);
+        a.invN = (float)(1.0 / ((double)it.spp * it.W * it.H));
+        a.img = it.out;
+        a.residual = 1;
+        a.seed_dev = b->d_seeds + i;
+        a.grid_q = grid_q;
+        a.W = br.W;
+        const uint32_t N = it.spp * (uint32_t)(it.W * it.H);
+        for (int g = 1; g <= 2 && e == cudaSuccess; ++g)
+            for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+                if (!(it.mask & (1u << t))) continue;
+                a.frame = g;
+                for (uint32_t r0 = 0; r0 < N && e == cudaSuccess; r0 += c.wave_roots) {
+                    a.root_begin = r0;
+                    a.root_end = std::min(N, r0 + c.wave_roots);
+                    e = launch_wave(techs[t], a, br.s);
+                }
+            }
+    }
+    for (rp_batch_s::Branch &br : b->br) {
+        if (e == cudaSuccess) e = cudaEventRecord(br.join, br.s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, br.join, 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    cudaStreamDestroy(cs);
+    b->graph = graph;
+    if (e != cudaSuccess) st = cuda_fail(e, "graph capture");
+    if (st == RP_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+        st = fail(RP_ERR_CUDA, "graph instantiation failed");
+    if (st == RP_OK) cudaGraphGetNodes(b->graph, nullptr, &b->nodes);
+    if (st != RP_OK) return bail(st);
+    *out = b;
+    return RP_OK;
+}
+
+}  // namespace
+
+extern "C" rp_status rp_batch_create(rp_scene *scene, const rp_batch_item *items, uint32_t n,
+                                     const rp_batch_config *config, rp_batch **out) {
+    if (!out) return fail(RP_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    return batch_build(scene, items, n, config, out);
+}
+
+extern "C" void rp_batch_destroy(rp_batch *batch) { delete batch; }
+
+extern "C" rp_status rp_batch_launch(rp_batch *batch, void *stream) {
+    if (!batch || !batch->exec) return fail(RP_ERR_INVALID_ARG, "null batch");
+    RP_CUDA(cudaGraphLaunch(batch->exec, (cudaStream_t)stream), "graph launch");
+    batch->sc->last_stream = (cudaStream_t)stream;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_batch_set_seeds(rp_batch *batch, const uint64_t *seeds, void *stream) {
+    if (!batch || !seeds) return fail(RP_ERR_INVALID_ARG, "null argument");
+    RP_CUDA(cudaMemcpyAsync(batch->d_seeds, seeds, sizeof(uint64_t) * batch->items.size(),
+                            cudaMemcpyHostToDevice, (cudaStream_t)stream),
+            "seed upload");
+    return RP_OK;
+}
+
+extern "C" rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *graph_nodes) {
+    if (!batch) return fail(RP_ERR_INVALID_ARG, "null batch");
+    if (config) *config = batch->cfg;
+    if (graph_nodes) *graph_nodes = batch->nodes;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *items, uint32_t n,
+                                       uint32_t spp_divisor, rp_batch_config *best, double *best_ms) {
+    if (!best) return fail(RP_ERR_INVALID_ARG, "null argument");
+    if (rp_status s = check_items(scene, items, n)) return s;
+    if (spp_divisor == 0) spp_divisor = 1;
+    // proxy items: spp / spp_divisor, all outputs into one scratch image
+    size_t px = 0;
+    uint64_t max_roots = 1;
+    std::vector<rp_batch_item> proxy(items, items + n);
+    for (rp_batch_item &it : proxy) {
+        it.spp = std::max(1u, it.spp / spp_divisor);
+        const size_t W = it.width ? it.width : (uint32_t)scene->S.W, H = it.height ? it.height : (uint32_t)scene->S.H;
+        px = std::max(px, W * H);
+        max_roots = std::max<uint64_t>(max_roots, (uint64_t)it.spp * W * H);
+    }
+    double *scratch = nullptr;
+    RP_CUDA(cudaMalloc((void **)&scratch, px * 3 * sizeof(double)), "cudaMalloc scratch");
+    for (rp_batch_item &it : proxy) it.d_out = scratch;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto measure = [&](const rp_batch_config &c, double &ms) -> rp_status {
+        rp_batch *b = nullptr;
+        if (rp_status s = batch_build(scene, proxy.data(), n, &c, &b)) return s;
+        float best_t = 1e30f;
+        cudaError_t e = cudaGraphLaunch(b->exec, st);            // warm-up
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, st);
+            e = cudaGraphLaunch(b->exec, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best_t = std::min(best_t, t);
+        }
+        delete b;
+        if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+        ms = best_t;
+        return RP_OK;
+    };
+    // coordinate descent from the defaults over the wave size, the number
+    // of concurrent branches and the blocks per SM of the queue kernels
+    std::vector<uint32_t> waves;
+    for (uint32_t w = 1u << 20; w <= (1u << 23); w <<= 1) {
+        waves.push_back(w);
+        if (w >= max_roots) break;
+    }
+    const std::vector<uint32_t> streams = {1, 2, 4};
+    const std::vector<uint32_t> bps = {8, 16, 32};
+    rp_batch_config cur{};
+    cur.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, scene->wave_cap);
+    cur.streams = 1;
+    cur.blocks_per_sm = 16;
+    double cur_ms = 0.0;
+    rp_status s = measure(cur, cur_ms);
+    for (int dim = 0; dim < 3 && s == RP_OK; ++dim) {
+        const std::vector<uint32_t> &vals = dim == 0 ? waves : dim == 1 ? streams : bps;
+        for (uint32_t v : vals) {
+            rp_batch_config c = cur;
+            (dim == 0 ? c.wave_roots : dim == 1 ? c.streams : c.blocks_per_sm) = v;
+            if (c.wave_roots == cur.wave_roots && c.streams == cur.streams && c.blocks_per_sm == cur.blocks_per_sm)
+                continue;
+            double ms = 0.0;
+            s = measure(c, ms);
+            if (s != RP_OK) break;
+            if (ms < cur_ms) { cur = c; cur_ms = ms; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(scratch);
+    if (s != RP_OK) return s;
+    *best = cur;
+    if (best_ms) *best_ms = cur_ms;
     return RP_OK;
 }

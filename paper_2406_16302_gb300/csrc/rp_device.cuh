@@ -113,6 +113,12 @@ enum { T_PT = 0, T_1 = 1, T_2 = 2, T_3 = 3, T_7 = 7 };
 enum { SD_ROOT = 0, SD_EYE = 1, SD_LIGHT = 2, SD_NEE = 3 };
 
 // four uniforms in [0, 1) on a 2^-24 grid, keyed by what they are used for
+// the launch's seed (batched launches read it from device memory so that a
+// captured graph can be replayed with new seeds)
+static __device__ __forceinline__ uint64_t lseed(const LaunchArgs &a) {
+    return a.seed_dev ? (uint64_t)*a.seed_dev : a.seed;
+}
+
 static __device__ __forceinline__ float4 draw(uint64_t seed, uint32_t root, int tech, int frame, int side,
                                        int step) {
     uint4 c = make_uint4(root, ((uint32_t)tech << 24) | ((uint32_t)frame << 20) |
@@ -453,9 +459,11 @@ static __device__ __forceinline__ float safe_rcp(float x) {
 }
 
 // closest (any = false) or first found (any = true) hit in one BVH
+// triangles with ids in [skip_lo, skip_lo + skip_n) are not there (the
+// moved object's base pose inside the static BVH)
 static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin, float &tmax, int ex0,
                          int ex1, bool any, Hit &h, int *stack, Counters &cnt,
-                         int *overflow) {
+                         int *overflow, int skip_lo = 0, int skip_n = 0) {
     if (B.n_nodes == 0) return false;
     const WtRay w = wt_setup(d);
     const float3 id = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -483,7 +491,7 @@ static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin,
                 ++cnt.tris;
                 const float4 v0 = __ldg(&B.tris[3 * i + 0]);
                 const int gid = __float_as_int(v0.w);
-                if (gid == ex0 || gid == ex1) continue;
+                if (gid == ex0 || gid == ex1 || (unsigned)(gid - skip_lo) < (unsigned)skip_n) continue;
                 const float4 v1 = __ldg(&B.tris[3 * i + 1]);
                 const float4 v2 = __ldg(&B.tris[3 * i + 2]);
                 float tt, bb1, bb2;
@@ -589,7 +597,8 @@ static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin
     const DevScene &S = c.A.S;
     bool found = false;
     if (!dyn_only) {
-        found = traverse(S.stat, o, d, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow);
+        found = traverse(S.stat, o, d, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow,
+                         c.A.E.skip_lo, c.A.E.skip_n);
         if (found && any) return true;
     }
     if (S.n_dyn > 0) {
@@ -1179,7 +1188,7 @@ static __device__ __forceinline__ bool vtx_black(const Ctx &c, int g, const Vtx 
 
 // (1) dynamic from emitter
 static __device__ void root_T1(Ctx &c, PathCounts &pc, int g, uint32_t root) {
-    const uint64_t seed = c.A.seed;
+    const uint64_t seed = lseed(c.A);
     const int D = c.A.S.max_depth;
     Vtx z[kMaxVerts];
     z[0] = sample_dynamic(c, g, draw(seed, root, T_1, g, SD_ROOT, 0));
@@ -1205,7 +1214,7 @@ static __device__ void root_T1(Ctx &c, PathCounts &pc, int g, uint32_t root) {
 
 // (2) dynamic from sensor
 static __device__ void root_T2(Ctx &c, PathCounts &pc, int g, uint32_t root) {
-    const uint64_t seed = c.A.seed;
+    const uint64_t seed = lseed(c.A);
     const int D = c.A.S.max_depth;
     Vtx yv[kMaxVerts];
     yv[0] = sample_dynamic(c, g, draw(seed, root, T_2, g, SD_ROOT, 0));
@@ -1230,7 +1239,7 @@ static __device__ void root_T2(Ctx &c, PathCounts &pc, int g, uint32_t root) {
 
 // (3) dynamic two ends
 static __device__ void root_T3(Ctx &c, PathCounts &pc, int g, uint32_t root) {
-    const uint64_t seed = c.A.seed;
+    const uint64_t seed = lseed(c.A);
     const int D = c.A.S.max_depth;
     if (D < 4) return;
     Vtx yv[kMaxVerts], zv[kMaxVerts], Lv[kMaxVerts];
@@ -1285,7 +1294,7 @@ static __device__ void root_T3(Ctx &c, PathCounts &pc, int g, uint32_t root) {
 // plain path tracing (frame-independent random numbers) when primal
 static __device__ void root_PT(Ctx &c, PathCounts &pc, int g, uint32_t root, bool residual) {
     const DevScene &S = c.A.S;
-    const uint64_t seed = c.A.seed;
+    const uint64_t seed = lseed(c.A);
     const int D = S.max_depth;
     const int tech = residual ? T_7 : T_PT;
     const int rg = residual ? g : 0;

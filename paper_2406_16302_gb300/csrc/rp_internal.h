@@ -57,6 +57,19 @@ struct DevEdit {
     float Minv[3][12];          // world -> object
     float mat[3][12];           // the dynamic object's material
     int motion;                 // M1 != M2
+    int object;                 // the moved object (0: the scene's dynamic mesh)
+    int skip_lo, skip_n;        // static triangles [skip_lo, skip_lo + skip_n) are the moved
+                                // object's base pose: static traversal skips them
+};
+
+// a movable object: its BVH in object space, triangles, area sampling table
+struct DevObject {
+    DevBVH bvh;
+    const float4 *tri;
+    const uint32_t *cdf;
+    int n;
+    float area;
+    int skip_lo, skip_n;
 };
 
 struct Record {
@@ -106,6 +119,8 @@ struct LaunchArgs {
     int frame;
     uint32_t root_begin, root_end;
     uint64_t seed;
+    const unsigned long long *seed_dev;   // if set, the seed is read from device memory
+    int grid_q;                 // blocks of the queue kernels (0: 16 per SM)
     float invN;                 // 1 / (spp * W * H)
     int tech_mask;
     double *img;                // accumulation image or null

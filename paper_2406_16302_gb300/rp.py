@@ -37,12 +37,23 @@ class rp_scene_desc(C.Structure):
                 ("materials", C.c_void_p), ("n_materials", C.c_uint32),
                 ("camera", C.c_float * 10), ("width", C.c_uint32), ("height", C.c_uint32),
                 ("max_depth", C.c_uint32), ("alpha_min", C.c_float), ("d_min", C.c_float),
-                ("jacobian_max", C.c_float)]
+                ("jacobian_max", C.c_float), ("n_objects", C.c_uint32),
+                ("object_ranges", C.c_void_p)]
 
 
 class rp_edit_desc(C.Structure):
     _fields_ = [("M1", C.c_float * 12), ("M2", C.c_float * 12),
-                ("mat1", C.c_float * 12), ("mat2", C.c_float * 12)]
+                ("mat1", C.c_float * 12), ("mat2", C.c_float * 12), ("object", C.c_uint32)]
+
+
+class rp_batch_item(C.Structure):
+    _fields_ = [("edit", C.c_void_p), ("width", C.c_uint32), ("height", C.c_uint32),
+                ("spp", C.c_uint32), ("seed", C.c_uint64), ("tech_mask", C.c_uint32),
+                ("d_out", C.c_void_p)]
+
+
+class rp_batch_config(C.Structure):
+    _fields_ = [("wave_roots", C.c_uint32), ("streams", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
 
 
 class rp_stats(C.Structure):
@@ -70,6 +81,8 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
            "rp_guide_create", "rp_guide_destroy", "rp_guide_set_weights", "rp_guide_get_weights",
            "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_loss_grad",
            "rp_guide_train_step", "rp_guide_status", "rp_scene_set_guide",
+           "rp_batch_create", "rp_batch_destroy", "rp_batch_launch", "rp_batch_set_seeds",
+           "rp_batch_info", "rp_batch_autotune",
            "rp_last_error"]
 
 GUIDE_WEIGHTS, GUIDE_IN, GUIDE_OUT = 20480, 80, 48
@@ -115,6 +128,12 @@ def lib():
         "rp_guide_train_step": (I, [P, C.c_float, P, P]),
         "rp_guide_status": (I, [P]),
         "rp_scene_set_guide": (I, [P, P]),
+        "rp_batch_create": (I, [P, P, U32, P, P]),
+        "rp_batch_destroy": (None, [P]),
+        "rp_batch_launch": (I, [P, P]),
+        "rp_batch_set_seeds": (I, [P, P, P]),
+        "rp_batch_info": (I, [P, P, P]),
+        "rp_batch_autotune": (I, [P, P, U32, U32, P, P]),
         "rp_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -149,6 +168,7 @@ def edit_desc(edit) -> rp_edit_desc:
     d.M2[:] = [float(v) for v in np.asarray(edit.M2, np.float32).ravel()]
     d.mat1[:] = [float(v) for v in np.asarray(edit.mat1, np.float32).ravel()]
     d.mat2[:] = [float(v) for v in np.asarray(edit.mat2, np.float32).ravel()]
+    d.object = int(getattr(edit, "object", 0))
     return d
 
 
@@ -180,6 +200,11 @@ class Scene:
         d.width, d.height = scene.camera.width, scene.camera.height
         d.max_depth = scene.max_depth
         d.alpha_min, d.d_min, d.jacobian_max = scene.alpha_min, scene.d_min, scene.jacobian_max
+        ranges = getattr(scene, "object_ranges", None)
+        if ranges is not None and len(ranges):
+            self._ranges = np.ascontiguousarray(ranges, np.uint32)
+            d.n_objects = len(self._ranges)
+            d.object_ranges = self._ranges.ctypes.data
         h = C.c_void_p()
         _check(lib().rp_scene_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -376,6 +401,72 @@ def rp_guide_status(guide: Guide):
 
 def rp_scene_set_guide(scene: Scene, guide):
     _check(lib().rp_scene_set_guide(scene.h, None if guide is None else guide.h))
+
+
+def _batch_items(items):
+    arr = (rp_batch_item * len(items))()
+    for i, (edit, w, h, spp, seed, mask, out) in enumerate(items):
+        arr[i].edit = edit.h.value
+        arr[i].width, arr[i].height = int(w), int(h)
+        arr[i].spp, arr[i].seed, arr[i].tech_mask = int(spp), int(seed), int(mask)
+        arr[i].d_out = out.data_ptr()
+    return arr
+
+
+class Batch:
+    """rp_batch_create / rp_batch_destroy.  items: list of
+    (Edit, width, height, spp, seed, tech_mask, float64 device image)."""
+
+    def __init__(self, scene: Scene, items, config=None):
+        self.items = list(items)          # keeps edits and images alive
+        arr = _batch_items(self.items)
+        h = C.c_void_p()
+        cfg = None
+        if config is not None:
+            cfg = rp_batch_config(*[int(v) for v in config])
+        _check(lib().rp_batch_create(scene.h, arr, len(self.items),
+                                     None if cfg is None else C.byref(cfg), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rp_batch_launch(batch: Batch, stream=None):
+    _check(lib().rp_batch_launch(batch.h, _stream(stream)))
+
+
+def rp_batch_set_seeds(batch: Batch, seeds, stream=None):
+    a = np.ascontiguousarray(seeds, dtype=np.uint64)
+    assert a.size == len(batch.items)
+    _check(lib().rp_batch_set_seeds(batch.h, a.ctypes.data_as(C.c_void_p), _stream(stream)))
+    if stream is None:
+        import torch
+        torch.cuda.current_stream().synchronize()
+
+
+def rp_batch_info(batch: Batch):
+    cfg = rp_batch_config()
+    nodes = C.c_uint64()
+    _check(lib().rp_batch_info(batch.h, C.byref(cfg), C.byref(nodes)))
+    return (cfg.wave_roots, cfg.streams, cfg.blocks_per_sm), int(nodes.value)
+
+
+def rp_batch_autotune(scene: Scene, items, spp_divisor=4):
+    arr = _batch_items(items)
+    cfg = rp_batch_config()
+    ms = C.c_double()
+    _check(lib().rp_batch_autotune(scene.h, arr, len(items), int(spp_divisor), C.byref(cfg),
+                                   C.byref(ms)))
+    return (cfg.wave_roots, cfg.streams, cfg.blocks_per_sm), float(ms.value)
 
 
 # ---------------------------------------------------------------------------

@@ -76,6 +76,8 @@ class Scene:
     d_min: float = 0.0346            # reconnection distance threshold (Sec. 5)
     jacobian_max: float = 10.0       # mapped-path Jacobian threshold (Sec. 5)
     name: str = ""
+    object_ranges: np.ndarray = None # (K, 2) uint32: movable objects 1..K as (first, count)
+                                     # ranges of the static triangles
 
     @property
     def n_static(self) -> int:
@@ -93,6 +95,7 @@ class Edit:
     mat1: np.ndarray                 # (12,) float32, dynamic object material in frame 1
     mat2: np.ndarray                 # (12,) float32, dynamic object material in frame 2
     name: str = ""
+    object: int = 0                  # 0: the dynamic mesh; k >= 1: movable object k
 
     @property
     def moves(self) -> bool:
@@ -585,3 +588,118 @@ def random_float_guide(seed, gain=1.0):
     for o, i in GUIDE_LAYER_SHAPES:
         out.append(rng.normal(0.0, gain * np.sqrt(2.0 / i), size=o * i))
     return bf16_round(np.concatenate(out).astype(np.float32)).astype(np.float64)
+
+
+# --- several movable objects and batches of edits ----------------------------
+
+def object_view(scene: Scene, k: int) -> Scene:
+    """The same geometry with movable object k (k >= 1) as the dynamic mesh
+    (its given coordinates as object space) and removed from the static
+    triangles; k = 0 returns the scene itself.  Only array slicing."""
+    if k == 0:
+        return scene
+    first, count = (int(v) for v in scene.object_ranges[k - 1])
+    tri = np.asarray(scene.static_triangles)
+    keep = np.ones(len(tri), dtype=bool)
+    keep[first:first + count] = False
+    ot = tri[first:first + count]
+    used, inv = np.unique(ot.ravel(), return_inverse=True)
+    return Scene(scene.static_vertices, tri[keep], np.asarray(scene.static_material)[keep],
+                 np.asarray(scene.static_vertices)[used], inv.reshape(-1, 3).astype(np.uint32),
+                 scene.materials, scene.camera, scene.max_depth, scene.alpha_min, scene.d_min,
+                 scene.jacobian_max, scene.name + f"_object{k}")
+
+
+def uv_sphere_fast(n_seg: int, n_ring: int):
+    """uv_sphere(n_seg, n_ring) built with array operations (same vertices and
+    triangles)."""
+    th = math.pi * np.arange(1, n_ring) / n_ring
+    ph = 2 * math.pi * np.arange(n_seg) / n_seg
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    ring = np.stack([np.sin(T) * np.cos(P), np.cos(T), np.sin(T) * np.sin(P)], -1).reshape(-1, 3)
+    verts = np.concatenate([[[0.0, 1.0, 0.0]], ring, [[0.0, -1.0, 0.0]]])
+    last = len(verts) - 1
+    s_ = np.arange(n_seg)
+    top = np.stack([np.zeros(n_seg, int), 1 + (s_ + 1) % n_seg, 1 + s_], 1)
+    r_ = np.arange(n_ring - 2)[:, None]
+    a = 1 + r_ * n_seg + s_[None, :]
+    a1 = 1 + r_ * n_seg + ((s_ + 1) % n_seg)[None, :]
+    b, b1 = a + n_seg, a1 + n_seg
+    mid = np.stack([np.stack([a, a1, b1], -1), np.stack([a, b1, b], -1)], 2).reshape(-1, 3)
+    base = 1 + (n_ring - 2) * n_seg
+    bot = np.stack([np.full(n_seg, last), base + s_, base + (s_ + 1) % n_seg], 1)
+    return verts, np.concatenate([top, mid, bot])
+
+
+def rigid_about(center, deg, axis, t) -> np.ndarray:
+    """Rotation by deg about a unit axis through center, then translation t."""
+    axis = np.asarray(axis, dtype=np.float64)
+    axis = axis / np.linalg.norm(axis)
+    a = math.radians(deg)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    R = np.eye(3) + math.sin(a) * K + (1 - math.cos(a)) * K @ K
+    c = np.asarray(center, dtype=np.float64)
+    M = np.zeros((3, 4))
+    M[:, :3] = R
+    M[:, 3] = c + np.asarray(t, dtype=np.float64) - R @ c
+    return M.astype(np.float32)
+
+
+def cfg4_batch(n_objects=32, seed=2406, min_tris=1000, max_tris=200000, max_depth=8,
+               resolutions=(256, 512, 1024), spp_range=(64, 256)):
+    """The cfg2 box and blob plus n_objects movable objects (displaced UV
+    spheres of log-uniform 1k..200k triangles, seeded Lambert albedo), and
+    one animation frame per object: an edit that moves it by a seeded rigid
+    transform (rotation <= 10 degrees about a random axis through its center,
+    translation <= 5% of the 2-unit extent), at a seeded resolution from
+    `resolutions` and a log-uniform spp in spp_range.
+    Returns (scene, [(edit, width, height, spp)])."""
+    rng = np.random.RandomState(seed)
+    base, _ = cfg2_box_blob(width=256, height=256, max_depth=max_depth, blob_level=5)
+    mats = list(base.materials)
+    verts = [np.asarray(base.static_vertices, np.float64)]
+    tris = [np.asarray(base.static_triangles, np.int64)]
+    mids = [np.asarray(base.static_material, np.int64)]
+    nv = len(verts[0])
+    nt = len(tris[0])
+    ranges, centers, albedos = [], [], []
+    for k in range(n_objects):
+        target = math.exp(rng.uniform(math.log(min_tris), math.log(max_tris)))
+        n_ring = max(4, int(round(math.sqrt(target / 4.0))))
+        n_seg = max(6, int(round(target / (2.0 * (n_ring - 1)))))
+        v, t = uv_sphere_fast(n_seg, n_ring)
+        r = rng.uniform(0.06, 0.14)
+        noise = value_noise_3d(v, 3.0, seed + 31 * k)
+        v = v * (r * (1.0 + 0.15 * noise))[:, None]
+        c = np.array([rng.uniform(-0.8, 0.8), rng.uniform(-0.85, 0.6), rng.uniform(-0.8, 0.6)])
+        alb = rng.uniform(0.2, 0.9, size=3)
+        m = len(mats)
+        mats.append(material(LAMBERT, tuple(alb)))
+        verts.append(v + c)
+        tris.append(t + nv)
+        mids.append(np.full(len(t), m))
+        ranges.append((nt, len(t)))
+        centers.append(c)
+        albedos.append(m)
+        nv += len(v)
+        nt += len(t)
+    scene = Scene(np.concatenate(verts).astype(np.float32), np.concatenate(tris).astype(np.uint32),
+                  np.concatenate(mids).astype(np.uint32), base.dyn_vertices, base.dyn_triangles,
+                  np.stack(mats).astype(np.float32), base.camera, max_depth,
+                  d_min=base.d_min, name="cfg4_batch",
+                  object_ranges=np.array(ranges, dtype=np.uint32))
+    frames = []
+    ident = translate((0.0, 0.0, 0.0))
+    for k in range(n_objects):
+        axis = rng.normal(size=3)
+        deg = rng.uniform(-10.0, 10.0)
+        tdir = rng.normal(size=3)
+        tdir *= rng.uniform(0.0, 0.1) / np.linalg.norm(tdir)
+        M2 = rigid_about(centers[k], deg, axis, tdir)
+        mrow = scene.materials[albedos[k]]
+        res = int(rng.choice(resolutions))
+        spp = int(round(math.exp(rng.uniform(math.log(spp_range[0]), math.log(spp_range[1])))))
+        e = Edit(ident.copy(), M2, mrow.copy(), mrow.copy(), name=f"move_object_{k + 1}",
+                 object=k + 1)
+        frames.append((e, res, res, spp))
+    return scene, frames
