@@ -467,6 +467,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2406_16302_gb300 import build, rp
+    from paper_2406_16302_gb300.dist import max_over_ranks
     if rank == 0 or ws == 1:
         build.build()
     if dist:
@@ -522,11 +523,7 @@ def main():
             dist.barrier()
     rp.rp_enable_timing(sc, False)
     my_ms = float(np.mean(step_ms))
-    worst_ms = my_ms
-    if dist:
-        t = torch.tensor([my_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        worst_ms = float(t.item())
+    worst_ms = max_over_ranks(my_ms, device="cuda")
     value = samples_per_step * ws / (worst_ms / 1e3)
     launches_per_step = sum(n for n, _ in kern.values()) / args.steps
 
@@ -543,10 +540,7 @@ def main():
             rp.rp_render_residual_host(sc, edit, spp, seed0 + 200 + k, host)
             times.append(time.perf_counter() - t0)
         e_ms = 1e3 * float(np.mean(times))
-        if dist:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e_ms, device="cuda")
         e2e = {"value": samples_per_step * ws / (e_ms / 1e3), "unit": "residual samples/s",
                "h2d_bytes_per_step": 4 * 48, "d2h_bytes_per_step": int(host.nbytes),
                "ms_per_step": e_ms}
