@@ -146,6 +146,23 @@ static bool material_ok(const float *m) {
     return true;
 }
 
+// conservative bounding sphere of a triangle table (vertices in .xyz)
+static float4 bounding_sphere(const std::vector<float4> &t) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (const float4 &v : t) {
+        const double p[3] = {v.x, v.y, v.z};
+        for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], p[a]); hi[a] = std::max(hi[a], p[a]); }
+    }
+    const double c[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+    double r2 = 0.0;
+    for (const float4 &v : t) {
+        const double d[3] = {v.x - c[0], v.y - c[1], v.z - c[2]};
+        r2 = std::max(r2, d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    const double r = std::sqrt(r2);
+    return make_float4((float)c[0], (float)c[1], (float)c[2], (float)(r * 1.001 + 1e-5));
+}
+
 extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
     if (!d || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
@@ -308,6 +325,8 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
         o0.cdf = S.dyn_cdf;
         o0.n = nd;
         o0.area = S.dyn_area;
+        o0.bs = bounding_sphere(dt);
+        S.dyn_bs = o0.bs;
         sc->objects.push_back(o0);
     }
     // movable objects: a BVH in object space (their given coordinates), the
@@ -347,6 +366,7 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
         o.bvh.n_tris = count;
         o.n = count;
         o.area = (float)oa;
+        o.bs = bounding_sphere(ot);
         o.skip_lo = first;
         o.skip_n = count;
         sc->objects.push_back(o);
@@ -460,6 +480,7 @@ static DevScene scene_for_edit(const rp_scene *sc, const DevEdit &E) {
     S.dyn_cdf = o.cdf;
     S.n_dyn = o.n;
     S.dyn_area = o.area;
+    S.dyn_bs = o.bs;
     return S;
 }
 

@@ -604,7 +604,12 @@ static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin
     if (S.n_dyn > 0) {
         const float *Mi = c.A.E.Minv[g];
         float3 oo = affine(Mi, o), dd = linear(Mi, d);
-        if (traverse(S.dyn, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow))
+        // a segment that misses the object's bounding sphere skips its BVH
+        const float3 co = f3(S.dyn_bs.x, S.dyn_bs.y, S.dyn_bs.z) - oo;
+        const float tc = fminf(fmaxf(dot3(co, dd), tmin), tmax);
+        const float3 q = co - dd * tc;
+        if (dot3(q, q) <= S.dyn_bs.w * S.dyn_bs.w &&
+            traverse(S.dyn, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow))
             found = true;
     }
     if (found && !any) refine_hit(c, g, o, d, h);
@@ -716,43 +721,78 @@ static __device__ __forceinline__ int camera_project(const DevScene &S, float3 p
 // path contribution (Eq. pathcontribution, pinhole importance), no visibility
 // ---------------------------------------------------------------------------
 
-// the factors are single precision; their product is accumulated in double
-// so that walks through near-coincident vertices (geometric terms of 1e8 and
-// more per edge) cannot overflow
-static __device__ double3 path_throughput(const Ctx &c, int g, const Vtx *x, int k, int &pix) {
+// A single-precision value with its own power-of-two exponent.  Walks
+// through near-coincident vertices (corners, crevices) make geometric terms
+// and area densities of 1e8 and more per edge, so path products overflow
+// plain single precision; the exponent is renormalised after each product.
+struct SF {
+    float m;
+    int e;
+};
+
+static __device__ __forceinline__ void sf_fix(float &m, int &e) {
+    const float a = fabsf(m);
+    if (a > 0x1p40f || (a < 0x1p-40f && a > 0.f)) {
+        int k;
+        m = frexpf(m, &k);
+        e += k;
+    }
+}
+
+static __device__ __forceinline__ SF sf_mul(SF a, float x) {
+    a.m *= x;
+    sf_fix(a.m, a.e);
+    return a;
+}
+
+static __device__ __forceinline__ SF sf_add(SF a, SF b) {
+    if (a.m == 0.f) return b;
+    if (b.m == 0.f) return a;
+    SF r = a.e >= b.e ? SF{a.m + ldexpf(b.m, b.e - a.e), a.e} : SF{b.m + ldexpf(a.m, a.e - b.e), b.e};
+    sf_fix(r.m, r.e);
+    return r;
+}
+
+static __device__ __forceinline__ float sf_val(SF a) { return ldexpf(a.m, a.e); }
+
+// path throughput f(x) (Eq. pathcontribution) as f * 2^e
+static __device__ float3 path_throughput(const Ctx &c, int g, const Vtx *x, int k, int &pix, int &e) {
     const DevScene &S = c.A.S;
+    e = 0;
     float cc;
     pix = camera_project(S, x[1].p, cc);
-    if (pix < 0) return d3(0.0, 0.0, 0.0);
+    if (pix < 0) return f3(0, 0, 0);
     float3 d01 = x[0].p - x[1].p;
     float r2 = dot3(d01, d01);
     float c1 = dot3(x[1].n, d01) / sqrtf(r2);
-    if (c1 <= 0.f) return d3(0.0, 0.0, 0.0);
+    if (c1 <= 0.f) return f3(0, 0, 0);
     float We = 1.0f / (S.pix_area * cc * cc * cc);
-    double s0 = (double)(We * c1) / (double)r2;
-    double3 f = d3(s0, s0, s0);
+    float s0 = We * c1 / r2;
+    float3 f = f3(s0, s0, s0);
     for (int j = 1; j <= k - 2; ++j) {
         float3 wi = unit3(x[j - 1].p - x[j].p);
-        float3 e = x[j + 1].p - x[j].p;
-        float r2e = dot3(e, e);
-        float3 wo = e * (1.0f / sqrtf(r2e));
+        float3 ed = x[j + 1].p - x[j].p;
+        float r2e = dot3(ed, ed);
+        float3 wo = ed * (1.0f / sqrtf(r2e));
         Mat m = get_mat(c, g, x[j].mat);
         float3 rho = bsdf_eval(m, x[j].n, wi, wo);
-        if (zero3(rho)) return d3(0.0, 0.0, 0.0);
+        if (zero3(rho)) return f3(0, 0, 0);
         float ca = dot3(x[j].n, wo), cb = -dot3(x[j + 1].n, wo);
-        if (ca <= 0.f || cb <= 0.f) return d3(0.0, 0.0, 0.0);
-        const double gt = (double)(ca * cb) / (double)r2e;
-        f = d3(f.x * rho.x * gt, f.y * rho.y * gt, f.z * rho.z * gt);
+        if (ca <= 0.f || cb <= 0.f) return f3(0, 0, 0);
+        f = mul3(f, rho) * (ca * cb);
+        f = f * (1.0f / r2e);
+        float mx = fmaxf(f.x, fmaxf(f.y, f.z));
+        if (mx > 0x1p40f || (mx < 0x1p-40f && mx > 0.f)) {
+            int kx;
+            frexpf(mx, &kx);
+            f = f * ldexpf(1.f, -kx);
+            e += kx;
+        }
     }
     Mat em = get_mat(c, g, x[k - 1].mat);
-    return d3(f.x * em.em.x, f.y * em.em.y, f.z * em.em.z);
+    return mul3(f, em.em);
 }
 
-static __device__ __forceinline__ bool zero3d(double3 a) { return a.x == 0.0 && a.y == 0.0 && a.z == 0.0; }
-
-static __device__ __forceinline__ float3 scale3d(double3 a, double s) {
-    return f3((float)(a.x * s), (float)(a.y * s), (float)(a.z * s));
-}
 
 // ---------------------------------------------------------------------------
 // technique densities (Sec. 4.1, 4.3): pE = forward (camera-to-light walk)
@@ -784,43 +824,45 @@ static __device__ float step_pdf(const Ctx &c, int g, const Vtx *x, int cond, in
     return area_from_dir(bsdf_pdf(m, x[at].n, wc, wo), x[at].p, x[to]);
 }
 
-// per-technique densities are products of single-precision factors
-// accumulated in double (see path_throughput)
-static __device__ double mis_denominator(const Ctx &c, int g, const Vtx *x, int k) {
+// the balance-heuristic denominator of a path: the sum over the enabled
+// techniques that can produce it of their area densities (Sec. 4.3), each a
+// product of single-precision factors kept as SF
+static __device__ SF mis_denominator(const Ctx &c, int g, const Vtx *x, int k) {
     const DevScene &S = c.A.S;
     const int tm = c.A.tech_mask;
     const bool t1 = tm & 1, t2 = tm & 2, t3 = tm & 4, t7 = tm & 8;
-    if (k == 2) return t7 ? pdf_camera_area(S, x[1]) : 0.0;
+    if (k == 2) return SF{t7 ? pdf_camera_area(S, x[1]) : 0.f, 0};
     float pE[kMaxVerts], pL[kMaxVerts];
-    const double pD = 1.0 / S.dyn_area, pLi = 1.0 / S.emit_area;
+    const float pD = 1.0f / S.dyn_area, pLi = 1.0f / S.emit_area;
     pE[1] = pdf_camera_area(S, x[1]);
     for (int j = 2; j <= k - 2; ++j) pE[j] = step_pdf(c, g, x, j - 2, j - 1, j);
     for (int j = 1; j <= k - 3; ++j) pL[j] = step_pdf(c, g, x, j + 2, j + 1, j);
-    double sum = 0.0;
+    SF sum{0.f, 0};
     if (t7) {
-        double p = pLi;
-        for (int j = 1; j <= k - 2; ++j) p *= pE[j];
-        sum += p;
+        SF p{pLi, 0};
+        for (int j = 1; j <= k - 2; ++j) p = sf_mul(p, pE[j]);
+        sum = sf_add(sum, p);
     }
     for (int i = 1; i <= k - 2; ++i) {
         if (!is_dyn(c, x[i])) continue;
         if (i == k - 2) {                    // (1) dynamic from emitter
             if (!t1) continue;
-            double p = pD * pLi;
-            for (int j = 1; j <= k - 3; ++j) p *= pL[j];
-            sum += p;
+            SF p{pD * pLi, 0};
+            for (int j = 1; j <= k - 3; ++j) p = sf_mul(p, pL[j]);
+            sum = sf_add(sum, p);
         } else if (i == 1) {                 // (2) dynamic from sensor
             if (!t2) continue;
-            double p = pD * pLi;
-            for (int j = 2; j <= k - 2; ++j) p *= pE[j];
-            sum += p;
+            SF p{pD * pLi, 0};
+            for (int j = 2; j <= k - 2; ++j) p = sf_mul(p, pE[j]);
+            sum = sf_add(sum, p);
         } else {                             // (3) dynamic two ends
             if (!t3) continue;
             float3 w = unit3(x[i + 1].p - x[i].p);
-            double p = pD * pLi * area_from_dir(cosine_pdf(x[i].n, w), x[i].p, x[i + 1]);
-            for (int j = i + 2; j <= k - 2; ++j) p *= pE[j];
-            for (int j = 1; j <= i - 1; ++j) p *= pL[j];
-            sum += p;
+            SF p{pD * pLi, 0};
+            p = sf_mul(p, area_from_dir(cosine_pdf(x[i].n, w), x[i].p, x[i + 1]));
+            for (int j = i + 2; j <= k - 2; ++j) p = sf_mul(p, pE[j]);
+            for (int j = 1; j <= i - 1; ++j) p = sf_mul(p, pL[j]);
+            sum = sf_add(sum, p);
         }
     }
     return sum;
@@ -1053,30 +1095,31 @@ struct PathCounts {
 // static_known: the caller already rejected static paths of technique (7)
 static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x, int n, uint32_t root,
                               int tech, int sa, int sb, bool residual, bool static_known = false) {
-    int pa;
-    const double3 fx = path_throughput(c, g, x, n, pa);
-    if (zero3d(fx)) return;
-    const double invN = c.A.invN;
+    int pa, ex;
+    const float3 fx = path_throughput(c, g, x, n, pa, ex);
+    if (zero3(fx)) return;
+    const float invN = c.A.invN;
     if (!residual) {               // primal path tracing: one technique
-        double p = 0.0;
+        SF p{0.f, 0};
         {
             // path tracing density alone
             const DevScene &S = c.A.S;
             if (n == 2) {
-                p = pdf_camera_area(S, x[1]);
+                p.m = pdf_camera_area(S, x[1]);
             } else {
-                p = (double)pdf_camera_area(S, x[1]) / S.emit_area;
-                for (int j = 2; j <= n - 2; ++j) p *= step_pdf(c, g, x, j - 2, j - 1, j);
+                p.m = pdf_camera_area(S, x[1]) / S.emit_area;
+                for (int j = 2; j <= n - 2; ++j) p = sf_mul(p, step_pdf(c, g, x, j - 2, j - 1, j));
             }
         }
         ++pc.paths;
-        emit(c, root, tech, g, sa, sb, pa, scale3d(fx, invN / p), -1, f3(0, 0, 0), 0, (float)p, 0.f, 1.f);
+        emit(c, root, tech, g, sa, sb, pa, fx * ldexpf(invN / p.m, ex - p.e), -1, f3(0, 0, 0), 0,
+             sf_val(p), 0.f, 1.f);
         return;
     }
     if (tech == T_7 && !static_known && path_is_static(c, g, x, n)) return;
     ++pc.paths;
-    const double Pg = mis_denominator(c, g, x, n);
-    const double sign = (g == 2) ? 1.0 : -1.0;
+    const SF Pg = mis_denominator(c, g, x, n);
+    const float sign = (g == 2) ? 1.0f : -1.0f;
     const int g2 = 3 - g;
     Vtx y[kMaxVerts];
     MapInfo mi;
@@ -1088,31 +1131,32 @@ static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x
     } else {
         map_path(c, g, g2, x, n, y, mi);
     }
-    double3 fy = d3(0.0, 0.0, 0.0);
-    int pb = -1;
-    double Py = 0.0;
+    float3 fy = f3(0, 0, 0);
+    int pb = -1, ey = 0;
+    SF Py{0.f, 0};
     if (mi.status == MAP_ACCEPT) {
         if (c.A.E.motion && !mapped_visible(c, g2, x, y, n, mi)) {
             mi.status = MAP_INVALID;
         } else {
-            fy = path_throughput(c, g2, y, n, pb);
-            if (zero3d(fy)) {
+            fy = path_throughput(c, g2, y, n, pb, ey);
+            if (zero3(fy)) {
                 mi.status = MAP_INVALID;
             } else {
                 Py = mis_denominator(c, g2, y, n);
-                if (!(Py > 0.0)) mi.status = MAP_INVALID;
+                if (!(Py.m > 0.f)) mi.status = MAP_INVALID;
             }
         }
     }
     if (mi.status == MAP_ACCEPT) {
         ++pc.accepted;
-        const double den = (Pg + Py * mi.J) / invN;
-        emit(c, root, tech, g, sa, sb, pa, scale3d(fx, sign / den), pb, scale3d(fy, -sign * mi.J / den),
-             mi.status, (float)Pg, (float)Py, mi.J);
+        const SF den = sf_add(Pg, SF{Py.m * mi.J, Py.e});
+        emit(c, root, tech, g, sa, sb, pa, fx * ldexpf(sign * invN / den.m, ex - den.e), pb,
+             fy * ldexpf(-sign * mi.J * invN / den.m, ey - den.e), mi.status, sf_val(Pg), sf_val(Py),
+             mi.J);
     } else {
         if (mi.status != MAP_INVALID) ++pc.rejected;
-        emit(c, root, tech, g, sa, sb, pa, scale3d(fx, sign * invN / Pg), -1, f3(0, 0, 0), mi.status,
-             (float)Pg, 0.f, 0.f);
+        emit(c, root, tech, g, sa, sb, pa, fx * ldexpf(sign * invN / Pg.m, ex - Pg.e), -1, f3(0, 0, 0),
+             mi.status, sf_val(Pg), 0.f, 0.f);
     }
 }
 

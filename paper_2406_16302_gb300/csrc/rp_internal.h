@@ -44,6 +44,8 @@ struct DevScene {
     const int *emit_ids;        // [n_emit] static triangle ids
     int n_static, n_dyn, n_emit, n_mats;
     float dyn_area, emit_area;
+    float4 dyn_bs;              // bounding sphere of the dynamic object (object space; radius
+                                // inflated so that the test is conservative)
     float3 cam_pos, cam_fwd, cam_right, cam_up;
     float hw, hh, pix_area, film_area;
     int W, H;
@@ -69,6 +71,7 @@ struct DevObject {
     const uint32_t *cdf;
     int n;
     float area;
+    float4 bs;                  // bounding sphere (object space, conservative)
     int skip_lo, skip_n;
 };
 
