@@ -52,7 +52,14 @@ typedef enum {
 #define RP_TECH_DYNAMIC_FROM_SENSOR  2u  /* (2): x_D seen by the sensor, walk to the lights */
 #define RP_TECH_DYNAMIC_TWO_ENDS     4u  /* (3): x_D, cosine light side, BSDF eye side */
 #define RP_TECH_PATH_TRACING         8u  /* path tracing with static paths rejected */
-#define RP_TECH_ALL                 15u
+#define RP_TECH_ALL                 15u  /* (1), (2), (3) and path tracing */
+/* ghost techniques (Sec. 4.2), for edits with motion: a point x_G sampled by
+ * area on the ghost (the edited object at its pose of the other frame) */
+#define RP_TECH_GHOST_FROM_EMITTER  16u  /* (4): the ray from x_L through x_G, walk to the sensor */
+#define RP_TECH_GHOST_FROM_SENSOR   32u  /* (5): the camera ray through x_G, walk to the lights */
+#define RP_TECH_GHOST_TWO_ENDS      64u  /* (6): rays from x_G along +w and -w, uniform w, walks */
+#define RP_TECH_GHOSTS             112u
+#define RP_TECH_SEVEN              127u
 
 /* Material row: 12 floats
  *   [type, albedo r g b, alpha, f0 r g b, emission r g b, unused]

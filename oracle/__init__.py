@@ -19,8 +19,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
-TECH_PT, TECH_T1, TECH_T2, TECH_T3, TECH_T7 = 0, 1, 2, 3, 7
+TECH_PT, TECH_T1, TECH_T2, TECH_T3, TECH_T4, TECH_T5, TECH_T6, TECH_T7 = 0, 1, 2, 3, 4, 5, 6, 7
 MASK_ALL = 0b1111                  # bit 0: T1, bit 1: T2, bit 2: T3, bit 3: T7
+MASK_GHOSTS = 0b1110000            # bit 4: T4, bit 5: T5, bit 6: T6 (ghost techniques)
+MASK_SEVEN = MASK_ALL | MASK_GHOSTS
 
 # status codes of a base path's mapping (see oracle.c)
 MAP_ACCEPT, MAP_INVALID, MAP_REJECT_NODYN, MAP_REJECT_MULTI, MAP_REJECT_INVERT, MAP_REJECT_JAC = \

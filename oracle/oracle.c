@@ -18,7 +18,9 @@
  *     [Sec. 3.4, Eq. difference_integral], estimated with the dynamic-vertex
  *     techniques (1) "dynamic from emitter", (2) "dynamic from sensor",
  *     (3) "dynamic two ends" [Sec. 4.1] plus path tracing with static paths
- *     rejected [Sec. 4.3], combined by the balance heuristic over all
+ *     rejected [Sec. 4.3], optionally the ghost techniques (4) "ghost from
+ *     emitter", (5) "ghost from sensor", (6) "ghost two ends" [Sec. 4.2],
+ *     combined by the balance heuristic over all
  *     techniques that can produce a path [Sec. 4.3], with the path mapping
  *     operators of Sec. 5 (object transform, reconnection, random replay,
  *     rejection) and two-way mapping [Sec. 5, "Path rejection"];
@@ -111,7 +113,8 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 }
 
 /* technique codes and random-number stream layout */
-enum { TECH_PT = 0, TECH_T1 = 1, TECH_T2 = 2, TECH_T3 = 3, TECH_T7 = 7 };
+enum { TECH_PT = 0, TECH_T1 = 1, TECH_T2 = 2, TECH_T3 = 3, TECH_T4 = 4, TECH_T5 = 5, TECH_T6 = 6,
+       TECH_T7 = 7 };
 enum { SIDE_ROOT = 0, SIDE_EYE = 1, SIDE_LIGHT = 2, SIDE_NEE = 3 };
 
 typedef struct { double u[4]; } rnd4;
@@ -650,10 +653,64 @@ static double step_pdf(const vtx *x, int cond, int at, int to) {
     return area_from_dir(bsdf_pdf(x[at].mat, x[at].n, wc, wo), x[at].p, &x[to]);
 }
 
-typedef struct { int t1, t2, t3, t7; } techmask;
+typedef struct { int t1, t2, t3, t7, t4, t5, t6; } techmask;
+
+/* ------------------------------------------------------------------------- */
+/* ghost crossings (Sec. 3.3, 4.2): where an edge of a frame-g path passes   */
+/* through the edited object's pose in the other frame                        */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { vec3 p, n; } gcross;
+
+/* every crossing of the open segment a-b of frame g with the ghost (the
+ * dynamic object at its pose of the other frame), up to max */
+static int ghost_crossings(const oscene *s, int g, vec3 a, vec3 b, gcross *out, int max) {
+    if (!s->motion || s->n_dyn == 0) return 0;
+    const int go = 3 - g;
+    vec3 e = sub(b, a);
+    double dist = length(e);
+    vec3 d = scale(e, 1.0 / dist);
+    const double tmin = s->eps, tmax = dist - s->eps;
+    const bvh *bv = &s->dyn_bvh[go];
+    int n = 0;
+    int stack[128];
+    int sp = 0;
+    if (bv->n_nodes == 0) return 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const bvh_node *nd = &bv->nodes[stack[--sp]];
+        if (!ray_box(a, d, nd->lo, nd->hi, tmin, tmax)) continue;
+        if (nd->left < 0) {
+            for (int i = nd->first; i < nd->first + nd->count; ++i) {
+                int lp = bv->index[i];
+                double t, u, v;
+                const tri *tr = &s->dyn_world[go][lp];
+                if (ray_tri(a, d, tr, &t, &u, &v) && t > tmin && t < tmax && n < max) {
+                    out[n].p = add(a, scale(d, t));
+                    out[n].n = tri_normal(tr);
+                    ++n;
+                }
+            }
+        } else {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
+    return n;
+}
+
+/* area density of x1 reached by the ray from o through the ghost point c,
+ * c sampled by area with density pD (Eq. vertex1pdf) */
+static double ghost_ray_pdf(double pD, vec3 o, const gcross *c, const vtx *x1) {
+    vec3 w = normalize(sub(x1->p, o));
+    double cg = fabs(dot(c->n, w)), c1 = fabs(dot(x1->n, w));
+    vec3 og = sub(c->p, o), o1 = sub(x1->p, o);
+    if (cg <= 0.0) return 0.0;
+    return pD * dot(og, og) / cg * c1 / dot(o1, o1);
+}
 
 /* sum over the enabled techniques that produce x of their per-root densities */
-static double mis_denominator(const oscene *s, const vtx *x, int k, techmask tm) {
+static double mis_denominator(const oscene *s, int g, const vtx *x, int k, techmask tm) {
     double pE[16], pL[16];
     double pD = 1.0 / s->dyn_area, pLi = 1.0 / s->emit_area;
     if (k == 2) return tm.t7 ? pdf_camera_area(s, &x[1]) : 0.0;
@@ -685,6 +742,37 @@ static double mis_denominator(const oscene *s, const vtx *x, int k, techmask tm)
             for (int j = i + 2; j <= k - 2; ++j) p *= pE[j];
             for (int j = 1; j <= i - 1; ++j) p *= pL[j];
             sum += p;
+        }
+    }
+    /* (4)-(6): one term per ghost crossing of an edge; (5) on the first edge,
+     * (4) on the last, (6) in between (Sec. 4.2, Eq. vertex1pdf and the
+     * two-ends geometric term with a uniform direction density 1 / (4 pi)) */
+    if ((tm.t4 || tm.t5 || tm.t6) && s->motion && k >= 3) {
+        for (int j = 0; j <= k - 2; ++j) {
+            const int kind = (j == 0) ? 5 : (j == k - 2) ? 4 : 6;
+            if ((kind == 4 && !tm.t4) || (kind == 5 && !tm.t5) || (kind == 6 && !tm.t6)) continue;
+            gcross cr[8];
+            int nc = ghost_crossings(s, g, x[j].p, x[j + 1].p, cr, 8);
+            for (int c = 0; c < nc; ++c) {
+                double p;
+                if (kind == 4) {
+                    p = pLi * ghost_ray_pdf(pD, x[k - 1].p, &cr[c], &x[k - 2]);
+                    for (int m = 1; m <= k - 3; ++m) p *= pL[m];
+                } else if (kind == 5) {
+                    p = pLi * ghost_ray_pdf(pD, x[0].p, &cr[c], &x[1]);
+                    for (int m = 2; m <= k - 2; ++m) p *= pE[m];
+                } else {
+                    vec3 w = normalize(sub(x[j + 1].p, x[j].p));
+                    vec3 e = sub(x[j + 1].p, x[j].p);
+                    double cg = fabs(dot(cr[c].n, w));
+                    if (cg <= 0.0) continue;
+                    p = pD * pLi * fabs(dot(x[j].n, w)) * fabs(dot(x[j + 1].n, w)) / (cg * dot(e, e)) /
+                        (4.0 * PI);
+                    for (int m = 1; m <= j - 1; ++m) p *= pL[m];
+                    for (int m = j + 2; m <= k - 2; ++m) p *= pE[m];
+                }
+                sum += p;
+            }
         }
     }
     return sum;
@@ -924,14 +1012,14 @@ static void evaluate_path(sink *k, int g, const vtx *x, int n, uint32_t root, in
     if (is_zero3(fx)) return;
     if (!k->residual) {
         /* primal path tracing: a single technique, no MIS */
-        techmask only7 = {0, 0, 0, 1};
-        double p = mis_denominator(s, x, n, only7);
+        techmask only7 = {0, 0, 0, 1, 0, 0, 0};
+        double p = mis_denominator(s, g, x, n, only7);
         emit(k, root, tech, g, sa, sb, pa, scale(fx, 1.0 / (k->N * p)), -1, v3(0, 0, 0), 0, p, 0,
              1);
         return;
     }
     if (tech == TECH_T7 && path_is_static(s, g, x, n)) { k->counters[0]++; return; }
-    double Pg = mis_denominator(s, x, n, k->tm);
+    double Pg = mis_denominator(s, g, x, n, k->tm);
     double sign = (g == 2) ? 1.0 : -1.0;
     int g2 = 3 - g;
     vtx y[16];
@@ -954,7 +1042,7 @@ static void evaluate_path(sink *k, int g, const vtx *x, int n, uint32_t root, in
         } else {
             fy = path_throughput(s, y, n, &pb);
             if (is_zero3(fy)) mi.status = MAP_INVALID;
-            else Py = mis_denominator(s, y, n, k->tm);
+            else Py = mis_denominator(s, g2, y, n, k->tm);
             if (!(Py > 0.0)) mi.status = MAP_INVALID;
         }
     }
@@ -1376,6 +1464,130 @@ static void root_T3(sink *k, int g, uint32_t root, uint64_t seed) {
     }
 }
 
+/* a point on the ghost: the dynamic object sampled by area at its pose of
+ * the other frame */
+static vtx sample_ghost(const oscene *s, int g, rnd4 r) {
+    vtx v = sample_dynamic(s, 3 - g, r);
+    v.prim = -1;                  /* not a surface of frame g */
+    v.dyn = 0;
+    return v;
+}
+
+/* (4) ghost from emitter: x_L by area, x_G on the ghost by area, the ray
+ * from x_L through x_G finds the first vertex, which walks to the sensor */
+static void root_T4(sink *k, int g, uint32_t root, uint64_t seed) {
+    const oscene *s = k->s;
+    if (!s->motion) return;
+    int D = s->max_depth;
+    vtx xG = sample_ghost(s, g, draw(seed, root, TECH_T4, g, SIDE_ROOT, 0));
+    vtx xL = sample_emitter(s, g, draw(seed, root, TECH_T4, g, SIDE_NEE, 0));
+    vec3 e = sub(xG.p, xL.p);
+    double dG = length(e);
+    vec3 w = scale(e, 1.0 / dG);
+    if (dot(xL.n, w) <= 0.0) return;
+    vtx z[16];
+    if (!trace_next(s, g, &xL, w, &z[0])) return;
+    if (length(sub(z[0].p, xL.p)) <= dG || dot(z[0].n, w) >= 0.0) return;
+    if (is_black(z[0].mat)) return;
+    vtx path[16];
+    for (int t = 0; t <= D - 2; ++t) {
+        if (t > 0) {
+            const vtx *prev = (t == 1) ? &xL : &z[t - 2];
+            if (!walk_step(s, g, prev, &z[t - 1], draw(seed, root, TECH_T4, g, SIDE_EYE, t), &z[t]))
+                break;
+            if (is_black(z[t].mat)) break;
+        }
+        if (camera_visible(s, g, &z[t])) {
+            int n = t + 3;
+            path[0] = camera_vertex(s);
+            for (int j = 0; j <= t; ++j) path[1 + j] = z[t - j];
+            path[n - 1] = xL;
+            evaluate_path(k, g, path, n, root, TECH_T4, t, 0);
+        }
+    }
+}
+
+/* (5) ghost from sensor: x_G on the ghost by area, the camera ray through
+ * x_G finds x_1, then path tracing with next-event estimation */
+static void root_T5(sink *k, int g, uint32_t root, uint64_t seed) {
+    const oscene *s = k->s;
+    if (!s->motion) return;
+    int D = s->max_depth;
+    vtx xG = sample_ghost(s, g, draw(seed, root, TECH_T5, g, SIDE_ROOT, 0));
+    double cc;
+    if (camera_project(s, xG.p, &cc) < 0) return;
+    vtx path[16];
+    path[0] = camera_vertex(s);
+    vec3 e = sub(xG.p, path[0].p);
+    double dG = length(e);
+    vec3 w = scale(e, 1.0 / dG);
+    if (!trace_next(s, g, &path[0], w, &path[1])) return;
+    if (length(sub(path[1].p, path[0].p)) <= dG || dot(path[1].n, w) >= 0.0) return;
+    for (int j = 1; j <= D - 1; ++j) {
+        if (is_black(path[j].mat)) break;
+        vtx L;
+        if (nee(s, g, &path[j], draw(seed, root, TECH_T5, g, SIDE_NEE, j), &L)) {
+            path[j + 1] = L;
+            evaluate_path(k, g, path, j + 2, root, TECH_T5, 0, j + 2);
+        }
+        if (j == D - 1) break;
+        if (!walk_step(s, g, &path[j - 1], &path[j], draw(seed, root, TECH_T5, g, SIDE_LIGHT, j),
+                       &path[j + 1]))
+            break;
+    }
+}
+
+/* (6) ghost two ends: x_G on the ghost by area and a uniform direction w;
+ * the rays from x_G along +w and -w find the light-side vertex y_1 and the
+ * eye-side vertex z_1 of an edge through x_G, then both sides walk */
+static void root_T6(sink *k, int g, uint32_t root, uint64_t seed) {
+    const oscene *s = k->s;
+    if (!s->motion) return;
+    int D = s->max_depth;
+    if (D < 3) return;
+    vtx xG = sample_ghost(s, g, draw(seed, root, TECH_T6, g, SIDE_ROOT, 0));
+    rnd4 r = draw(seed, root, TECH_T6, g, SIDE_ROOT, 1);
+    double zc = 1.0 - 2.0 * r.u[0], rs = sqrt(fmax(0.0, 1.0 - zc * zc)), phi = 2.0 * PI * r.u[1];
+    vec3 w = v3(rs * cos(phi), rs * sin(phi), zc);
+    vtx yv[16], zv[16], Lv[16];
+    int Lok[16], Cok[16];
+    if (!trace_next(s, g, &xG, w, &yv[1]) || dot(yv[1].n, w) >= 0.0 || is_black(yv[1].mat)) return;
+    if (!trace_next(s, g, &xG, scale(w, -1.0), &zv[1]) || dot(zv[1].n, w) <= 0.0 ||
+        is_black(zv[1].mat))
+        return;
+    int ny = 1, nz = 1;
+    for (int t = 2; t <= D - 2; ++t) {
+        const vtx *prev = (t == 2) ? &zv[1] : &yv[t - 2];
+        if (!walk_step(s, g, prev, &yv[t - 1], draw(seed, root, TECH_T6, g, SIDE_LIGHT, t), &yv[t]))
+            break;
+        if (is_black(yv[t].mat)) break;
+        ny = t;
+    }
+    for (int t = 1; t <= ny; ++t)
+        Lok[t] = nee(s, g, &yv[t], draw(seed, root, TECH_T6, g, SIDE_NEE, t), &Lv[t]);
+    for (int t = 2; t <= D - 2; ++t) {
+        const vtx *prev = (t == 2) ? &yv[1] : &zv[t - 2];
+        if (!walk_step(s, g, prev, &zv[t - 1], draw(seed, root, TECH_T6, g, SIDE_EYE, t), &zv[t]))
+            break;
+        if (is_black(zv[t].mat)) break;
+        nz = t;
+    }
+    for (int t = 1; t <= nz; ++t) Cok[t] = camera_visible(s, g, &zv[t]);
+    vtx path[16];
+    for (int te = 1; te <= nz; ++te) {
+        if (!Cok[te]) continue;
+        for (int sl = 1; sl <= ny && te + sl <= D - 1; ++sl) {
+            if (!Lok[sl]) continue;
+            int n = te + sl + 2;
+            path[0] = camera_vertex(s);
+            for (int j = 0; j < te; ++j) path[1 + j] = zv[te - j];
+            for (int j = 1; j <= sl; ++j) path[te + j] = yv[j];
+            path[n - 1] = Lv[sl];
+            evaluate_path(k, g, path, n, root, TECH_T6, te, sl);
+        }
+    }
+}
+
 /* path tracing with next-event estimation (technique PT / (7)) */
 static void root_PT(sink *k, int g, uint32_t root, uint64_t seed, int tech) {
     const oscene *s = k->s;
@@ -1523,8 +1735,10 @@ void oracle_destroy(void *h) {
     free(s);
 }
 
+/* technique mask bits: 0 (1), 1 (2), 2 (3), 3 path tracing, 4 (4), 5 (5), 6 (6) */
 static techmask mask_from(int m) {
-    techmask t = {(m >> 0) & 1, (m >> 1) & 1, (m >> 2) & 1, (m >> 3) & 1};
+    techmask t = {(m >> 0) & 1, (m >> 1) & 1, (m >> 2) & 1, (m >> 3) & 1,
+                  (m >> 4) & 1, (m >> 5) & 1, (m >> 6) & 1};
     return t;
 }
 
@@ -1535,6 +1749,9 @@ static void run_roots(sink *k, int tech, int g, uint32_t r0, uint32_t r1, uint64
         case TECH_T1: root_T1(k, g, r, seed); break;
         case TECH_T2: root_T2(k, g, r, seed); break;
         case TECH_T3: root_T3(k, g, r, seed); k->vscale = 0.0; break;
+        case TECH_T4: root_T4(k, g, r, seed); break;
+        case TECH_T5: root_T5(k, g, r, seed); break;
+        case TECH_T6: root_T6(k, g, r, seed); break;
         case TECH_T7: root_PT(k, g, r, seed, TECH_T7); break;
         default: root_PT(k, g, r, seed, TECH_PT); break;
         }
@@ -1551,9 +1768,9 @@ int oracle_render_residual(void *h, uint32_t spp, uint64_t seed, uint32_t r0, ui
     memset(&k, 0, sizeof k);
     k.s = s; k.img = img; k.N = (double)spp * s->W * s->H;
     k.tm = mask_from(tech_mask); k.residual = 1;
-    const int techs[4] = {TECH_T1, TECH_T2, TECH_T3, TECH_T7};
+    const int techs[7] = {TECH_T1, TECH_T2, TECH_T3, TECH_T7, TECH_T4, TECH_T5, TECH_T6};
     for (int g = 1; g <= 2; ++g)
-        for (int t = 0; t < 4; ++t)
+        for (int t = 0; t < 7; ++t)
             if ((tech_mask >> t) & 1) run_roots(&k, techs[t], g, r0, r1, seed);
     if (counters) memcpy(counters, k.counters, sizeof k.counters);
     return 0;

@@ -179,6 +179,33 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                     if (dot3(xD.n, w) > 0.f) push_closest(A, 0, 0, xD.p, w, xD.prim, make_tag(r, SIDE_LIGHT, 1));
                 }
             }
+        } else if (T == T_4 || T == T_5 || T == T_6) {
+            // ghost techniques: a point on the ghost (the object at its pose
+            // of the other frame) by area (Sec. 4.2)
+            const Vtx xG = sample_dynamic(c, 3 - g, draw(lseed(A), root, T, g, SD_ROOT, 0));
+            if (T == T_4) {
+                const Vtx xL = sample_emitter(c, g, draw(lseed(A), root, T_4, g, SD_NEE, 0));
+                store_vtx(W, 1, r, xL);
+                const float3 w = unit3(xG.p - xL.p);
+                if (dot3(xL.n, w) > 0.f) push_closest(A, 0, 0, xL.p, w, xL.prim, make_tag(r, SIDE_ROOT, 0));
+            } else if (T == T_5) {
+                float cc;
+                if (camera_project(A.S, xG.p, cc) >= 0)
+                    push_closest(A, 0, 0, A.S.cam_pos, unit3(xG.p - A.S.cam_pos), -1,
+                                 make_tag(r, SIDE_ROOT, 0));
+            } else if (D >= 3) {
+                // two rays from x_G along a uniform direction w and along -w
+                Vtx g0 = xG;
+                g0.prim = -1;
+                store_vtx(W, 0, r, g0);
+                const float4 u = draw(lseed(A), root, T_6, g, SD_ROOT, 1);
+                const double zc = 1.0 - 2.0 * (double)u.x, rs = sqrt(fmax(0.0, 1.0 - zc * zc));
+                double sp, cp;
+                sincos2pi(A.S, u.y, sp, cp);
+                const float3 w = tof(d3(rs * cp, rs * sp, zc));
+                push_closest(A, 0, 0, xG.p, w, -1, make_tag(r, SIDE_LIGHT, 1));
+                push_closest(A, 0, 0, xG.p, w * -1.f, -1, make_tag(r, SIDE_EYE, 1));
+            }
         } else {
             // path tracing: a stratified camera ray through pixel root mod (W H)
             const int tech = A.residual ? T_7 : T_PT;
@@ -299,6 +326,7 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
     const int tech = (T == T_PT) ? (A.residual ? T_7 : T_PT) : T;
     const int rg = (T == T_PT && !A.residual) ? 0 : g;
     const bool ghosts = (T == T_PT) && A.residual && A.E.motion;
+    constexpr bool camera_walk = (T == T_PT || T == T_5);      // x_1 from the camera, NEE at every vertex
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int prim = W.h_prim[i];
         if (prim < 0) continue;
@@ -310,7 +338,22 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
         Vtx v = make_vertex_at(c, g, prim, W.h_b1[i], W.h_b2[i],
                                f3(W.h_p[i], W.h_p[W.qc + i], W.h_p[2 * W.qc + i]));
         if (dot3(v.n, d) >= 0.f) continue;                     // back face
-        if (T == T_PT) {
+        if ((T == T_4 || T == T_5) && side == SIDE_ROOT) {
+            // the first vertex must lie behind the ghost point on its ray
+            const Vtx xG = sample_dynamic(c, 3 - g, draw(lseed(A), root, T, g, SD_ROOT, 0));
+            const float3 o = (T == T_4) ? load_vtx(c, W, 1, r).p : A.S.cam_pos;
+            if (len3(v.p - o) <= len3(xG.p - o)) continue;
+        }
+        if (T == T_4 && side == SIDE_ROOT) {
+            // technique (4): x_1 from x_L through the ghost, then as technique (1)
+            if (vtx_black(c, g, v)) continue;
+            store_vtx(W, 0, r, v);
+            W.flags[r] = RF_ROOT_OK;
+            if (in_image_facing(c, v)) push_shadow(A, it + 1, v, camera_vertex(c), make_tag(r, CK_CAMERA, 0));
+            if (D - 2 >= 1) continue_walk(c, out, it, r, load_vtx(c, W, 1, r), v, T_4, g, SD_EYE, 1);
+            continue;
+        }
+        if (camera_walk) {
             // x_{j} with j = 1 (camera hit) or j = m + 1 (walk step m)
             const int j = (side == SIDE_ROOT) ? 1 : m + 1;
             store_vtx(W, j == 1 ? 0 : slot_light(D, m), r, v);
@@ -327,15 +370,30 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
             if (j < D - 1) continue_walk(c, out, it, r, prev, v, tech, rg, SD_LIGHT, j);
             continue;
         }
+        // the previous vertex of a walk's first vertex: x_D, or for technique (6)
+        // the ghost point (on the same line as the other first vertex)
+        auto first_prev = [&]() -> Vtx {
+            if (T == T_6) {
+                Vtx p;
+                const size_t i0 = r;
+                p.p = f3(W.px[i0], W.py[i0], W.pz[i0]);
+                p.n = f3(0.f, 0.f, 0.f);
+                p.prim = -1;
+                p.mat = kMatCamera;
+                p.b1 = p.b2 = 0.f;
+                return p;
+            }
+            return load_vtx(c, W, 0, r);
+        };
         if (vtx_black(c, g, v)) continue;
         if (side == SIDE_EYE) {
             // techniques (1) and (3): eye-side walk vertex z_m
             store_vtx(W, slot_eye(D, m), r, v);
             W.len_eye[r] = m;
             if (in_image_facing(c, v)) push_shadow(A, it + 1, v, camera_vertex(c), make_tag(r, CK_CAMERA, m));
-            const int last = (T == T_1) ? D - 2 : D - 3;
+            const int last = (T == T_1 || T == T_4 || T == T_6) ? D - 2 : D - 3;
             if (m < last) {
-                Vtx prev = load_vtx(c, W, m == 1 ? 0 : slot_eye(D, m - 1), r);
+                Vtx prev = m == 1 ? first_prev() : load_vtx(c, W, slot_eye(D, m - 1), r);
                 continue_walk(c, out, it, r, prev, v, T, g, SD_EYE, m + 1);
             }
         } else {
@@ -345,8 +403,8 @@ __global__ void __launch_bounds__(256) k_extend(const __grid_constant__ LaunchAr
             Vtx L = sample_emitter(c, g, draw(lseed(A), root, T, g, SD_NEE, m));
             store_vtx(W, slot_nee(D, m), r, L);
             if (faces(v, L.p) && faces(L, v.p)) push_shadow(A, it + 1, v, L, make_tag(r, CK_NEE, m));
-            const int last = (T == T_2) ? D - 2 : D - 3;
-            Vtx prev = load_vtx(c, W, m == 1 ? 0 : slot_light(D, m - 1), r);
+            const int last = (T == T_2 || T == T_6) ? D - 2 : D - 3;
+            Vtx prev = m == 1 ? first_prev() : load_vtx(c, W, slot_light(D, m - 1), r);
             if (m < last) continue_walk(c, out, it, r, prev, v, T, g, SD_LIGHT, m + 1);
             if (T == T_3 && m == 1) {
                 // the eye side of (3) starts at x_D, conditioned on y_1
@@ -440,7 +498,14 @@ __device__ int assemble(const Ctx &c, uint32_t r, int tech, int sa, int sb, Vtx 
     const WaveBuf &W = c.A.W;
     const int D = c.A.S.max_depth;
     x[0] = camera_vertex(c);
-    if (tech == T_1) {                       // (cam, z_t, ..., z_1, x_D, x_L), t = sa
+    if (tech == T_6) {                       // (cam, z_te..z_1, y_1..y_sl, L_sl)
+        const int te = sa, sl = sb;
+        for (int j = 0; j < te; ++j) x[1 + j] = load_vtx(c, W, slot_eye(D, te - j), r);
+        for (int j = 1; j <= sl; ++j) x[te + j] = load_vtx(c, W, slot_light(D, j), r);
+        x[te + sl + 1] = load_vtx(c, W, slot_nee(D, sl), r);
+        return te + sl + 2;
+    }
+    if (tech == T_1 || tech == T_4) {        // (cam, z_t, ..., z_1, x_D, x_L), t = sa
         const int t = sa;
         for (int j = 0; j < t; ++j) x[1 + j] = load_vtx(c, W, slot_eye(D, t - j), r);
         x[t + 1] = load_vtx(c, W, 0, r);
@@ -488,10 +553,20 @@ __global__ void __launch_bounds__(128) k_enum(const __grid_constant__ LaunchArgs
         ++roots;
         const uint32_t cam = W.cam_ok[r], nee = W.nee_ok[r];
         // enumerate the non-static base paths into mapping tasks
-        if (T == T_1) {
+        if (T == T_1 || T == T_4) {
             if (!(W.flags[r] & RF_ROOT_OK)) continue;
             for (int t = 0; t <= W.len_eye[r]; ++t)
-                if (cam & (1u << t)) dispatch_path(c, pc, x, 0, r, T_1, t, 0);
+                if (cam & (1u << t)) dispatch_path(c, pc, x, 0, r, T, t, 0);
+        } else if (T == T_5) {
+            for (int j = 1; j <= W.len_light[r]; ++j)
+                if (nee & (1u << j)) dispatch_path(c, pc, x, 0, r, T_5, 0, j + 2);
+        } else if (T == T_6) {
+            const int nz = W.len_eye[r], ny = W.len_light[r];
+            for (int te = 1; te <= nz; ++te) {
+                if (!(cam & (1u << te))) continue;
+                for (int sl = 1; sl <= ny && te + sl <= D - 1; ++sl)
+                    if (nee & (1u << sl)) dispatch_path(c, pc, x, 0, r, T_6, te, sl);
+            }
         } else if (T == T_2) {
             if (!(W.flags[r] & RF_ROOT_OK)) continue;
             for (int s2 = 1; s2 <= W.len_light[r]; ++s2)
@@ -590,7 +665,8 @@ __global__ void __launch_bounds__(kBlock) k_map(const __grid_constant__ LaunchAr
     Vtx x[kMaxVerts];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int4 t = A.W.tasks[i];
-        const int k = assemble(c, (uint32_t)t.x, t.y == T_7 ? T_PT : t.y, t.z, t.w, x);
+        const int lay = (t.y == T_7 || t.y == T_5) ? T_PT : t.y;   // slot layout of the technique
+        const int k = assemble(c, (uint32_t)t.x, lay, t.z, t.w, x);
         evaluate_path(c, pc, A.frame, x, k, A.root_begin + (uint32_t)t.x, t.y, t.z, t.w, true, true);
     }
     if (A.stats) {
@@ -690,11 +766,17 @@ cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
         RP_LAUNCH("k_trace_shadow", gQ, kBlock, k_trace_shadow, a, it + 1);
     }
     const int gE = grid_for(n, 128, 1 << 20);
-    if (a.residual && a.E.motion) {
+    if constexpr (T == T_4 || T == T_5 || T == T_6) {
+        // ghost techniques exist only with motion: always mapped
         RP_LAUNCH("k_enum", gE, 128, k_enum<T>, a);
         RP_LAUNCH("k_map", gQ, kBlock, k_map, a);
     } else {
-        RP_LAUNCH("k_eval", gE, 128, k_eval_fast<T>, a);
+        if (a.residual && a.E.motion) {
+            RP_LAUNCH("k_enum", gE, 128, k_enum<T>, a);
+            RP_LAUNCH("k_map", gQ, kBlock, k_map, a);
+        } else {
+            RP_LAUNCH("k_eval", gE, 128, k_eval_fast<T>, a);
+        }
     }
     return cudaGetLastError();
 }
@@ -706,6 +788,9 @@ cudaError_t launch_wave(int tech, const LaunchArgs &a, cudaStream_t s) {
     case 1: return run_wave<T_1>(a, s);
     case 2: return run_wave<T_2>(a, s);
     case 3: return run_wave<T_3>(a, s);
+    case 4: return a.E.motion ? run_wave<T_4>(a, s) : cudaSuccess;
+    case 5: return a.E.motion ? run_wave<T_5>(a, s) : cudaSuccess;
+    case 6: return a.E.motion ? run_wave<T_6>(a, s) : cudaSuccess;
     case 7:
     case 0: return run_wave<T_PT>(a, s);
     default: return cudaErrorInvalidValue;

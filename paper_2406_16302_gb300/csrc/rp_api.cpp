@@ -544,7 +544,7 @@ static rp_status check_render(rp_scene *sc, uint32_t spp, uint32_t mask) {
     if (spp == 0) return fail(RP_ERR_INVALID_ARG, "spp must be positive");
     if ((uint64_t)spp * sc->S.W * sc->S.H > 0xffffffffull)
         return fail(RP_ERR_INVALID_ARG, "spp * width * height must fit in 32 bits");
-    if (mask == 0 || (mask & ~RP_TECH_ALL)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
+    if (mask == 0 || (mask & ~RP_TECH_SEVEN)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
     return RP_OK;
 }
 
@@ -651,10 +651,12 @@ static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint6
     if (sc->guide && (mask & RP_TECH_DYNAMIC_TWO_ENDS))
         RP_CUDA(cudaMemsetAsync(sc->guide->smp.wt, 0, sizeof(float) * sc->guide->cap, st),
                 "memset guide weights");
-    const int techs[4] = {1, 2, 3, 7};
+    // mask bits 0..6: techniques (1), (2), (3), path tracing, (4), (5), (6);
+    // the ghost techniques need motion (without it there is no ghost)
+    const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
     for (int g = 1; g <= 2; ++g)
-        for (int t = 0; t < 4; ++t) {
-            if (!(mask & (1u << t))) continue;
+        for (int t = 0; t < 7; ++t) {
+            if (!(mask & (1u << t)) || (t >= 4 && !E.motion)) continue;
             a.frame = g;
             if (rp_status s = run_waves(sc, a, techs[t], 0, N, st)) return s;
         }
@@ -666,6 +668,8 @@ static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint6
 // scratch memory besides the image
 static rp_status render_into_direct(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
                                     uint32_t mask, double *d_out, cudaStream_t st) {
+    if (mask & RP_TECH_GHOSTS)
+        return fail(RP_ERR_UNSUPPORTED, "the one-thread-per-root kernels have no ghost techniques");
     LaunchArgs a = base_args(sc, E, spp, seed, mask);
     a.G = GuideLaunch{};           // the one-thread-per-root kernels run without the proposal
     a.img = d_out;
@@ -760,8 +764,8 @@ extern "C" rp_status rp_dump_samples(rp_scene *scene, const rp_edit_handle *edit
                                      uint64_t capacity, unsigned long long *d_count, void *stream) {
     if (rp_status s = check_render(scene, spp, tech_mask)) return s;
     if (!edit || !d_count || (!d_records && capacity)) return fail(RP_ERR_INVALID_ARG, "null buffer");
-    if (tech != 1 && tech != 2 && tech != 3 && tech != 7)
-        return fail(RP_ERR_INVALID_ARG, "tech must be 1, 2, 3 or 7");
+    if (tech < 1 || tech > 7)
+        return fail(RP_ERR_INVALID_ARG, "tech must be in 1..7");
     if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
     if (root_end < root_begin || root_end > spp * (uint32_t)(scene->S.W * scene->S.H))
         return fail(RP_ERR_INVALID_ARG, "root range out of bounds");
@@ -1208,7 +1212,7 @@ int device_sms() {
     return n > 0 ? n : 152;
 }
 
-int popcount4(uint32_t m) { return (int)(m & 1) + (int)((m >> 1) & 1) + (int)((m >> 2) & 1) + (int)((m >> 3) & 1); }
+int popcount4(uint32_t m) { return __builtin_popcount(m & 127u); }
 
 rp_status check_items(rp_scene *sc, const rp_batch_item *items, uint32_t n) {
     if (!sc || !items || n == 0) return fail(RP_ERR_INVALID_ARG, "null scene, null items or no items");
@@ -1219,7 +1223,7 @@ rp_status check_items(rp_scene *sc, const rp_batch_item *items, uint32_t n) {
         if (W == 0 || H == 0 || W * H > (1u << 26)) return fail(RP_ERR_INVALID_ARG, "item image size out of range");
         if (it.spp == 0 || (uint64_t)it.spp * W * H > 0xffffffffull)
             return fail(RP_ERR_INVALID_ARG, "item spp must be positive and spp * width * height fit in 32 bits");
-        if (it.tech_mask == 0 || (it.tech_mask & ~RP_TECH_ALL)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
+        if (it.tech_mask == 0 || (it.tech_mask & ~RP_TECH_SEVEN)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
     }
     return RP_OK;
 }
@@ -1290,7 +1294,7 @@ rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, cons
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, cs);
     for (rp_batch_s::Branch &br : b->br)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(br.s, b->fork, 0);
-    const int techs[4] = {1, 2, 3, 7};
+    const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
     const int grid_q = (int)c.blocks_per_sm * device_sms();
     for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
         const rp_batch_s::Item &it = b->items[i];
@@ -1308,8 +1312,8 @@ rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, cons
         a.W = br.W;
         const uint32_t N = it.spp * (uint32_t)(it.W * it.H);
         for (int g = 1; g <= 2 && e == cudaSuccess; ++g)
-            for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
-                if (!(it.mask & (1u << t))) continue;
+            for (int t = 0; t < 7 && e == cudaSuccess; ++t) {
+                if (!(it.mask & (1u << t)) || (t >= 4 && !it.E.motion)) continue;
                 a.frame = g;
                 for (uint32_t r0 = 0; r0 < N && e == cudaSuccess; r0 += c.wave_roots) {
                     a.root_begin = r0;

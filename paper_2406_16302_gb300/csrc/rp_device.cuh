@@ -109,7 +109,7 @@ static __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-enum { T_PT = 0, T_1 = 1, T_2 = 2, T_3 = 3, T_7 = 7 };
+enum { T_PT = 0, T_1 = 1, T_2 = 2, T_3 = 3, T_4 = 4, T_5 = 5, T_6 = 6, T_7 = 7 };
 enum { SD_ROOT = 0, SD_EYE = 1, SD_LIGHT = 2, SD_NEE = 3 };
 
 // four uniforms in [0, 1) on a 2^-24 grid, keyed by what they are used for
@@ -616,6 +616,98 @@ static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin
     return found;
 }
 
+// every hit of a ray with t in (tmin, tmax) in one BVH, up to maxh (the
+// ghost crossings of an edge); returns the number found
+static __device__ int traverse_all(const DevBVH &B, float3 o, float3 d, float tmin, float tmax,
+                                   float *ts, int *prims, int maxh, int *stack, Counters &cnt,
+                                   int *overflow) {
+    if (B.n_nodes == 0) return 0;
+    const WtRay w = wt_setup(d);
+    const float3 id = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float3 oid = f3(o.x * id.x, o.y * id.y, o.z * id.z);
+    int sp = 0, node = 0, n = 0;
+    for (;;) {
+        ++cnt.nodes;
+        const float4 na = __ldg(&B.nodes[4 * node + 0]);
+        const float4 nb = __ldg(&B.nodes[4 * node + 1]);
+        const float4 nc = __ldg(&B.nodes[4 * node + 2]);
+        const float4 nd = __ldg(&B.nodes[4 * node + 3]);
+        const int c0 = __float_as_int(nd.x), c1 = __float_as_int(nd.y);
+        float t0, t1;
+        const bool h0 = box_hit(na.x, na.y, na.z, na.w, nc.x, nc.y, id, oid, tmin, tmax, t0);
+        const bool h1 = box_hit(nb.x, nb.y, nb.z, nb.w, nc.z, nc.w, id, oid, tmin, tmax, t1);
+        for (int side = 0; side < 2; ++side) {
+            const bool hs = side ? h1 : h0;
+            const int cs = side ? c1 : c0;
+            if (!hs || cs >= 0) continue;
+            const int first = ~cs;
+            const int count = __float_as_int(side ? nd.w : nd.z);
+            for (int i = first; i < first + count; ++i) {
+                ++cnt.tris;
+                const float4 v0 = __ldg(&B.tris[3 * i + 0]);
+                const float4 v1 = __ldg(&B.tris[3 * i + 1]);
+                const float4 v2 = __ldg(&B.tris[3 * i + 2]);
+                float tmx = tmax, tt, bb1, bb2;
+                if (tri_hit(w, o, xyz(v0), xyz(v1), xyz(v2), tmin, tmx, tt, bb1, bb2) && n < maxh) {
+                    ts[n] = tt;
+                    prims[n] = __float_as_int(v0.w);
+                    ++n;
+                }
+            }
+        }
+        const bool g0 = h0 && c0 >= 0, g1 = h1 && c1 >= 0;
+        if (g0 && g1) {
+            if (sp < kStackDepth) {
+                stack[sp * kBlock] = c1;
+                ++sp;
+            } else {
+                *overflow = 1;
+            }
+            node = c0;
+        } else if (g0) {
+            node = c0;
+        } else if (g1) {
+            node = c1;
+        } else {
+            if (sp == 0) break;
+            --sp;
+            node = stack[sp * kBlock];
+        }
+    }
+    return n;
+}
+
+constexpr int kMaxCross = 8;        // ghost crossings kept per edge
+
+// crossings of the open segment a-b of frame g with the ghost: the edited
+// object at its pose of the other frame (Sec. 3.3); positions and unit
+// normals in world space
+static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, float3 *cp, float3 *cn) {
+    const DevScene &S = c.A.S;
+    if (!c.A.E.motion || S.n_dyn == 0) return 0;
+    const int go = 3 - g;
+    const float3 e = b - a;
+    const float dist = len3(e);
+    const float3 d = e * (1.0f / dist);
+    const float tmin = S.eps, tmax = dist - S.eps;
+    const float *Mi = c.A.E.Minv[go];
+    const float3 oo = affine(Mi, a), dd = linear(Mi, d);
+    const float3 co = f3(S.dyn_bs.x, S.dyn_bs.y, S.dyn_bs.z) - oo;
+    const float tc = fminf(fmaxf(dot3(co, dd), tmin), tmax);
+    const float3 q = co - dd * tc;
+    if (dot3(q, q) > S.dyn_bs.w * S.dyn_bs.w) return 0;
+    float ts[kMaxCross];
+    int prims[kMaxCross];
+    const int n = traverse_all(S.dyn, oo, dd, tmin, tmax, ts, prims, kMaxCross, c.stack, c.cnt,
+                               &c.overflow);
+    for (int i = 0; i < n; ++i) {
+        cp[i] = a + d * ts[i];
+        const int q3 = 3 * (prims[i] - S.n_static);
+        cn[i] = linear(c.A.E.M[go], f3(S.dyn_tri[q3].w, S.dyn_tri[q3 + 1].w, S.dyn_tri[q3 + 2].w));
+    }
+    return n;
+}
+
 // ---------------------------------------------------------------------------
 // path vertices
 // ---------------------------------------------------------------------------
@@ -827,7 +919,7 @@ static __device__ float step_pdf(const Ctx &c, int g, const Vtx *x, int cond, in
 // the balance-heuristic denominator of a path: the sum over the enabled
 // techniques that can produce it of their area densities (Sec. 4.3), each a
 // product of single-precision factors kept as SF
-static __device__ SF mis_denominator(const Ctx &c, int g, const Vtx *x, int k) {
+static __device__ SF mis_denominator(Ctx &c, int g, const Vtx *x, int k) {
     const DevScene &S = c.A.S;
     const int tm = c.A.tech_mask;
     const bool t1 = tm & 1, t2 = tm & 2, t3 = tm & 4, t7 = tm & 8;
@@ -863,6 +955,47 @@ static __device__ SF mis_denominator(const Ctx &c, int g, const Vtx *x, int k) {
             for (int j = i + 2; j <= k - 2; ++j) p = sf_mul(p, pE[j]);
             for (int j = 1; j <= i - 1; ++j) p = sf_mul(p, pL[j]);
             sum = sf_add(sum, p);
+        }
+    }
+    // (4)-(6): one term per ghost crossing of an edge, (5) on the first
+    // edge, (4) on the last, (6) in between (Sec. 4.2: the area density of
+    // the vertex behind a ghost point sampled by area, Eq. vertex1pdf, and
+    // the two-ends geometric term with a uniform direction density 1 / 4 pi)
+    if ((tm & 0x70) && c.A.E.motion && k >= 3) {
+        for (int j = 0; j <= k - 2; ++j) {
+            const int kind = (j == 0) ? 5 : (j == k - 2) ? 4 : 6;
+            if (!(tm & (1 << kind))) continue;
+            float3 cp[kMaxCross], cn[kMaxCross];
+            const int nc = ghost_crossings(c, g, x[j].p, x[j + 1].p, cp, cn);
+            for (int q = 0; q < nc; ++q) {
+                SF p{pD * pLi, 0};
+                if (kind == 4 || kind == 5) {
+                    const float3 o = (kind == 4) ? x[k - 1].p : x[0].p;
+                    const Vtx &x1 = (kind == 4) ? x[k - 2] : x[1];
+                    const float3 w = unit3(x1.p - o);
+                    const float cg = fabsf(dot3(cn[q], w)), c1 = fabsf(dot3(x1.n, w));
+                    if (!(cg > 0.f)) continue;
+                    const float3 og = cp[q] - o, o1 = x1.p - o;
+                    p = sf_mul(p, dot3(og, og) / cg);
+                    p = sf_mul(p, c1 / dot3(o1, o1));
+                    if (kind == 4) {
+                        for (int m = 1; m <= k - 3; ++m) p = sf_mul(p, pL[m]);
+                    } else {
+                        for (int m = 2; m <= k - 2; ++m) p = sf_mul(p, pE[m]);
+                    }
+                } else {
+                    const float3 e = x[j + 1].p - x[j].p;
+                    const float3 w = unit3(e);
+                    const float cg = fabsf(dot3(cn[q], w));
+                    if (!(cg > 0.f)) continue;
+                    p = sf_mul(p, fabsf(dot3(x[j].n, w)) * fabsf(dot3(x[j + 1].n, w)) /
+                                      (cg * 4.0f * kPi));
+                    p = sf_mul(p, 1.0f / dot3(e, e));
+                    for (int m = 1; m <= j - 1; ++m) p = sf_mul(p, pL[m]);
+                    for (int m = j + 2; m <= k - 2; ++m) p = sf_mul(p, pE[m]);
+                }
+                sum = sf_add(sum, p);
+            }
         }
     }
     return sum;

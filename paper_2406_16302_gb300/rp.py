@@ -18,6 +18,8 @@ LIB_PATH = os.environ.get("RP_LIBRARY") or os.path.join(HERE, "_build", "librp.s
 
 RP_OK = 0
 RP_TECH_ALL = 15
+RP_TECH_GHOSTS = 112           # techniques (4), (5), (6)
+RP_TECH_SEVEN = 127
 STATUS = {0: "RP_OK", 1: "RP_ERR_INVALID_ARG", 2: "RP_ERR_OOM", 3: "RP_ERR_CUDA",
           4: "RP_ERR_TIMEOUT", 5: "RP_ERR_UNSUPPORTED"}
 
