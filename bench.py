@@ -208,6 +208,79 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Displacement sweep on the cfg1 box (the sphere translated by d along
+    x): equal-time residual MSE of the residual estimator with the camera
+    mapping (default), the object-transform mapping and without mapping, with
+    the four and with all seven techniques, of correlated
+    path tracing and of re-rendering frame 2, against a converged reference
+    (trend only; the paper's own table is on its scenes)."""
+    import torch
+    from paper_2406_16302_gb300 import build, rp, scenes
+    build.build()
+    rp.lib()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    spp, K, R = 16, 4, 16
+    rows = []
+    for d in (0.02, 0.05, 0.1, 0.2, 0.4):
+        scene, edit = scenes.cfg1_box_sphere(width=128, height=128, max_depth=6)
+        edit.M2 = edit.M1.copy()
+        edit.M2[0, 3] += d
+        sc = rp.Scene(scene)
+        ed = rp.Edit(sc, edit)
+
+        def residual(s_, seed, mask, mapping=2):
+            rp.rp_scene_set_mapping(sc, mapping)
+            out = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+            t = timed(lambda: rp.rp_render_residual(sc, ed, s_, seed, out, tech_mask=mask, stream=stream))
+            rp.rp_scene_set_mapping(sc, 2)
+            return out, t
+
+        def primal(frame, s_, seed):
+            out = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+            return out, timed(lambda: rp.rp_render_primal(sc, ed, frame, s_, seed, out, stream=stream))
+
+        ref = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+        for i in range(R):
+            ref += residual(4 * spp, 800000 + i, 127)[0]
+        ref /= R
+        row = {"displacement": d}
+        budget = None
+        for name, mask, mapping in (("camera_4", 15, 2), ("object_4", 15, 1), ("off_4", 15, 0),
+                                    ("camera_7", 127, 2), ("object_7", 127, 1)):
+            ms, ts = [], []
+            for k in range(K):
+                img, t = residual(spp, 810000 + 10 * k, mask, mapping)
+                ms.append(float(((img - ref) ** 2).mean().item()))
+                ts.append(t)
+            t = float(np.mean(ts))
+            budget = budget or t
+            row[name] = {"mse": float(np.mean(ms)), "ms": t, "mse_at_budget": float(np.mean(ms)) * t / budget}
+        ms, ts = [], []
+        for k in range(K):
+            i2, ta = primal(2, spp, 820000 + k)
+            i1, tb = primal(1, spp, 820000 + k)
+            ms.append(float(((i2 - i1 - ref) ** 2).mean().item()))
+            ts.append(ta + tb)
+        t = float(np.mean(ts))
+        row["correlated_pt"] = {"spp": spp, "mse": float(np.mean(ms)), "ms": t,
+                                "mse_at_budget": float(np.mean(ms)) * t / budget}
+        rows.append(row)
+    print(json.dumps({"experiment": "displacement_sweep", "scene": "cfg1_box_sphere 128x128, max depth 6",
+                      "spp": spp, "repeats": K, "reference": f"all seven techniques, {R} x {4 * spp} spp",
+                      "rows": rows}), flush=True)
+
+
 def equal_time_mse(rp, sc, ed, scene, spp, K=4, ref_renders=16, guide_iters=30, guide_lr=1e-2):
     """Equal-time residual MSE against a converged reference (the plain
     method at ref_renders x 4 x spp, averaged over independent seeds).  Each
@@ -456,6 +529,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch_32_edits":
         return run_batch(args)
+    if args.workload == "sweep_displacement":
+        return run_sweep(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -377,6 +377,22 @@ rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *grap
 rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *items, uint32_t n,
                             uint32_t spp_divisor, rp_batch_config *best, double *best_ms);
 
+/* Path mapping (Sec. 5) for the renders of a scene that follow:
+ *   RP_MAPPING_CAMERA (2, default): paths whose first edge is dynamic (x_1 on
+ *     the object, or the camera ray to x_1 crossing the ghost) keep their
+ *     camera direction (Sec. 5, "Mapping between the dynamic and ghost pair")
+ *     and map their light side as technique (2) does; all others move their
+ *     dynamic vertex with the object;
+ *   RP_MAPPING_OBJECT (1): the object transform for every path;
+ *   RP_MAPPING_OFF (0): no mapping; a base path of frame g adds
+ *     s_g f_g(x) / (N P_g(x)), so each frame's dynamic paths are estimated by
+ *     that frame's sampling alone (the "without path mapping" comparison).
+ * All three are unbiased.  Edits without motion are unaffected. */
+#define RP_MAPPING_OFF 0
+#define RP_MAPPING_OBJECT 1
+#define RP_MAPPING_CAMERA 2
+rp_status rp_scene_set_mapping(rp_scene *scene, int mode);
+
 /* Thread-local message describing the last error (empty string if none). */
 const char *rp_last_error(void);
 

@@ -25,8 +25,8 @@ MASK_GHOSTS = 0b1110000            # bit 4: T4, bit 5: T5, bit 6: T6 (ghost tech
 MASK_SEVEN = MASK_ALL | MASK_GHOSTS
 
 # status codes of a base path's mapping (see oracle.c)
-MAP_ACCEPT, MAP_INVALID, MAP_REJECT_NODYN, MAP_REJECT_MULTI, MAP_REJECT_INVERT, MAP_REJECT_JAC = \
-    range(6)
+MAP_ACCEPT, MAP_INVALID, MAP_REJECT_NODYN, MAP_REJECT_MULTI, MAP_REJECT_INVERT, MAP_REJECT_JAC, \
+    MAP_OFF = range(7)
 
 RECORD_DTYPE = np.dtype([
     ("root", "<u4"), ("tech", "<i4"), ("frame", "<i4"), ("sa", "<i4"), ("sb", "<i4"),
@@ -59,6 +59,7 @@ def lib():
                                     C.c_double]
         L.oracle_set_edit.argtypes = [P, P, P, P, P]
         L.oracle_set_brute_force.argtypes = [P, C.c_int]
+        L.oracle_set_mapping.argtypes = [P, C.c_int]
         L.oracle_destroy.argtypes = [P]
         L.oracle_render_residual.argtypes = [P, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32,
                                              C.c_int, P, P]
@@ -222,6 +223,11 @@ class Oracle:
                 for a in (edit.M1, edit.M2, edit.mat1, edit.mat2)]
         self._edit = arrs
         lib().oracle_set_edit(self.h, *[_p(a) for a in arrs])
+
+    def set_mapping(self, mode):
+        """Path mapping: 2 camera replay for dynamic first edges (default), 1 the
+        object transform only, 0 / False off (each frame estimates its own paths)."""
+        lib().oracle_set_mapping(self.h, int(mode))
 
     def set_guide(self, guide):
         """Attach an integer network (W, shift, out_exp, box) to technique (3); None detaches."""

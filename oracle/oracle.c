@@ -176,6 +176,7 @@ typedef struct {
     bvh stat_bvh;
     bvh dyn_bvh[3];
     int brute_force;
+    int map_mode;        /* 0: no mapping, 1: object transform only, 2: camera replay (default) */
     /* sampling tables */
     double *dyn_cdf;     /* over dyn_obj areas */
     double dyn_area;
@@ -820,7 +821,8 @@ enum {
     MAP_REJECT_NODYN = 2,   /* only dynamic edges: the identity image is blocked */
     MAP_REJECT_MULTI = 3,   /* more than one dynamic vertex */
     MAP_REJECT_INVERT = 4,  /* the inverse mapping would not replay this step */
-    MAP_REJECT_JAC = 5
+    MAP_REJECT_JAC = 5,
+    MAP_OFF = 6             /* path mapping switched off: each frame estimates its own paths */
 };
 
 static int reconnect_ok(const oscene *s, const vtx *a, const vtx *ap, const vtx *b) {
@@ -884,12 +886,49 @@ static int map_step(const oscene *s, int g2, const vtx *x, vtx *y, int a, int b,
     return MAP_ACCEPT;
 }
 
+/* the first edge of a frame-g path is dynamic: x_1 lies on the object or the
+ * camera ray to x_1 crosses the ghost (the object at its other-frame pose) */
+static int first_edge_dynamic(const oscene *s, int g, const vtx *x, int k) {
+    if (k < 2 || !s->motion) return 0;
+    if (x[1].dyn) return 1;
+    return !segment_clear(s, 3 - g, &x[0], &x[1], 1);
+}
+
+/* camera replay (Sec. 5, "Mapping between the dynamic and ghost pair": the
+ * same camera direction in both frames): y_1 is the first hit of the camera
+ * ray through x_1 in frame g2 (area Jacobian: the ratio of the camera
+ * densities), then the light side walks as for technique (2).  The class of
+ * paths with a dynamic first edge is closed under this map. */
+static void map_camera(const oscene *s, int g, int g2, const vtx *x, int k, vtx *y, mapinfo *mi) {
+    for (int j = 2; j <= k - 2; ++j)
+        if (x[j].dyn) { mi->status = MAP_REJECT_MULTI; return; }
+    vec3 w = normalize(sub(x[1].p, x[0].p));
+    vtx y1;
+    if (!trace_next(s, g2, &y[0], w, &y1) || dot(y1.n, w) >= 0.0) { mi->status = MAP_INVALID; return; }
+    y[1] = y1;
+    mi->replayed[1] = 1;
+    double px = pdf_camera_area(s, &x[1]), py = pdf_camera_area(s, &y[1]);
+    if (!(px > 0.0) || !(py > 0.0)) { mi->status = MAP_INVALID; return; }
+    mi->J *= px / py;
+    for (int b = 2; b <= k - 2; ++b) {
+        int st = map_step(s, g2, x, y, b - 1, b, b - 2, mi);
+        if (st != MAP_ACCEPT) { mi->status = st; return; }
+    }
+    if (!first_edge_dynamic(s, g2, y, k)) { mi->status = MAP_REJECT_INVERT; return; }
+    (void)g;
+    if (!(mi->J <= s->jac_max && 1.0 / mi->J <= s->jac_max)) { mi->status = MAP_REJECT_JAC; return; }
+    mi->status = MAP_ACCEPT;
+}
+
 /* map the frame-g path x (k vertices) into frame g2 */
 static void map_path(const oscene *s, int g, int g2, const vtx *x, int k, vtx *y, mapinfo *mi) {
-    (void)g;
     mi->J = 1.0;
     for (int j = 0; j < k; ++j) mi->replayed[j] = 0;
     for (int j = 0; j < k; ++j) y[j] = x[j];
+    if (s->map_mode == 2 && first_edge_dynamic(s, g, x, k)) {
+        map_camera(s, g, g2, x, k, y, mi);
+        return;
+    }
     int nd = 0, i = -1;
     for (int j = 1; j <= k - 2; ++j)
         if (x[j].dyn) { ++nd; i = j; }
@@ -928,6 +967,12 @@ static void map_path(const oscene *s, int g, int g2, const vtx *x, int k, vtx *y
     }
     if (!(mi->J <= s->jac_max && 1.0 / mi->J <= s->jac_max)) {
         mi->status = MAP_REJECT_JAC;
+        return;
+    }
+    /* the image must stay outside the camera-replay class, else the inverse
+     * map would differ */
+    if (s->map_mode == 2 && first_edge_dynamic(s, g2, y, k)) {
+        mi->status = MAP_REJECT_INVERT;
         return;
     }
     mi->status = MAP_ACCEPT;
@@ -1033,6 +1078,8 @@ static void evaluate_path(sink *k, int g, const vtx *x, int n, uint32_t root, in
             if (y[j].kind == VK_SURFACE) y[j].mat = prim_mat(s, g2, y[j].prim);
         }
         mi.status = MAP_ACCEPT; mi.J = 1.0;
+    } else if (s->map_mode == 0) {
+        mi.status = MAP_OFF; mi.J = 0.0;
     } else {
         map_path(s, g, g2, x, n, y, &mi);
     }
@@ -1046,7 +1093,7 @@ static void evaluate_path(sink *k, int g, const vtx *x, int n, uint32_t root, in
             if (!(Py > 0.0)) mi.status = MAP_INVALID;
         }
     }
-    k->counters[1 + (mi.status < 6 ? mi.status : 5)]++;
+    k->counters[1 + (mi.status < 6 ? mi.status : 6)]++;
     if (mi.status == MAP_ACCEPT) {
         double J = mi.J;
         double den = k->N * (Pg + Py * J);
@@ -1639,6 +1686,7 @@ void *oracle_create(const float *sv, int n_sv, const uint32_t *st, const uint32_
                     int max_depth, double alpha_min, double d_min, double jac_max) {
     (void)n_sv; (void)n_dv;
     oscene *s = (oscene *)calloc(1, sizeof(oscene));
+    s->map_mode = 2;
     s->n_static = n_st;
     s->n_dyn = n_dt;
     s->stat = (tri *)malloc(sizeof(tri) * (size_t)(n_st > 0 ? n_st : 1));
@@ -1722,6 +1770,12 @@ int oracle_set_edit(void *h, const float *M1, const float *M2, const float *mat1
 }
 
 void oracle_set_brute_force(void *h, int on) { ((oscene *)h)->brute_force = on; }
+
+/* path mapping mode: 2 (default) camera replay for paths whose first edge
+ * is dynamic, else the object transform; 1 the object transform for every
+ * path; 0 no mapping (a base path of frame g adds s_g f_g(x) / (N P_g(x))
+ * and each frame's paths come from its own sampling) */
+void oracle_set_mapping(void *h, int mode) { ((oscene *)h)->map_mode = mode; }
 
 void oracle_destroy(void *h) {
     oscene *s = (oscene *)h;
@@ -1920,8 +1974,13 @@ static void check_pair(const oscene *s, int g, const vtx *x, int n) {
         double ay = length(cross(sub(py4[0], py4[1]), sub(py4[2], py4[3])));
         int a, c;
         replay_geometry(x, n, b, &a, &c);
+        const int cam_rule = s->map_mode == 2 && first_edge_dynamic(s, g, x, n);
+        if (cam_rule) { a = b - 1; c = b - 2; }
         double pxd, pyd;
-        if (c < 0) {
+        if (cam_rule && b == 1) {
+            pxd = pdf_camera_area(s, &x[1]);
+            pyd = pdf_camera_area(s, &y[1]);
+        } else if (c < 0) {
             pxd = area_from_dir(cosine_pdf(x[a].n, normalize(sub(x[b].p, x[a].p))), x[a].p, &x[b]);
             pyd = area_from_dir(cosine_pdf(y[a].n, normalize(sub(y[b].p, y[a].p))), y[a].p, &y[b]);
         } else {

@@ -101,6 +101,7 @@ struct rp_scene_s {
     uint32_t wave_cap = 1u << 22;  // roots per wave
     KernelTimer timer;
     bool timing_on = false;
+    int map_mode = 2;                 // path mapping mode (rp_scene_set_mapping)
     // learned proposal of technique (3) and its per-root buffers
     rp_guide *guide = nullptr;
     int8_t *gin = nullptr;
@@ -521,6 +522,7 @@ static LaunchArgs base_args(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64
     a.tech_mask = (int)mask;
     a.stats = sc->stats_on ? sc->d_stats : nullptr;
     a.residual = 1;
+    a.map_mode = sc->map_mode;
     a.timer = sc->timing_on ? &sc->timer : nullptr;
     if (rp_guide *gd = sc->guide) {
         a.G.on = 1;
@@ -1450,5 +1452,12 @@ extern "C" rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *ite
     if (s != RP_OK) return s;
     *best = cur;
     if (best_ms) *best_ms = cur_ms;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_scene_set_mapping(rp_scene *scene, int mode) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    if (mode < 0 || mode > 2) return fail(RP_ERR_INVALID_ARG, "mapping mode must be 0, 1 or 2");
+    scene->map_mode = mode;
     return RP_OK;
 }

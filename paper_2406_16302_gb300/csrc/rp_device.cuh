@@ -681,8 +681,13 @@ constexpr int kMaxCross = 8;        // ghost crossings kept per edge
 
 // crossings of the open segment a-b of frame g with the ghost: the edited
 // object at its pose of the other frame (Sec. 3.3); positions and unit
-// normals in world space
-static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, float3 *cp, float3 *cn) {
+// normals in world space.  The normals are taken in double from the
+// triangle's world-space vertices, and each crossing point is re-solved in
+// double on the plane of the triangle the traversal found: the ghost
+// densities divide by |n . w|, and near the silhouette (where area sampling
+// of the ghost puts many samples) both that and the crossing's place on the
+// edge are ill-conditioned in single precision.
+static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, double3 *cp, double3 *cn) {
     const DevScene &S = c.A.S;
     if (!c.A.E.motion || S.n_dyn == 0) return 0;
     const int go = 3 - g;
@@ -700,10 +705,17 @@ static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, float3 
     int prims[kMaxCross];
     const int n = traverse_all(S.dyn, oo, dd, tmin, tmax, ts, prims, kMaxCross, c.stack, c.cnt,
                                &c.overflow);
+    const double3 da = d3(a), dw = dunit(dsub(d3(b), da));
     for (int i = 0; i < n; ++i) {
-        cp[i] = a + d * ts[i];
         const int q3 = 3 * (prims[i] - S.n_static);
-        cn[i] = linear(c.A.E.M[go], f3(S.dyn_tri[q3].w, S.dyn_tri[q3 + 1].w, S.dyn_tri[q3 + 2].w));
+        const float *M = c.A.E.M[go];
+        const double3 v0 = daffine(M, d3(S.dyn_tri[q3])), v1 = daffine(M, d3(S.dyn_tri[q3 + 1])),
+                      v2 = daffine(M, d3(S.dyn_tri[q3 + 2]));
+        const double3 nn = dcross(dsub(v1, v0), dsub(v2, v0));
+        const double den = ddot(nn, dw);
+        const double t = den != 0.0 ? ddot(nn, dsub(v0, da)) / den : (double)ts[i];
+        cp[i] = dadd(da, dscale(dw, t));
+        cn[i] = dunit(nn);
     }
     return n;
 }
@@ -837,6 +849,15 @@ static __device__ __forceinline__ SF sf_mul(SF a, float x) {
     return a;
 }
 
+// product with a double factor of any magnitude
+static __device__ __forceinline__ SF sf_mul_d(SF a, double x) {
+    int k;
+    a.m *= (float)frexp(x, &k);
+    a.e += k;
+    sf_fix(a.m, a.e);
+    return a;
+}
+
 static __device__ __forceinline__ SF sf_add(SF a, SF b) {
     if (a.m == 0.f) return b;
     if (b.m == 0.f) return a;
@@ -965,32 +986,30 @@ static __device__ SF mis_denominator(Ctx &c, int g, const Vtx *x, int k) {
         for (int j = 0; j <= k - 2; ++j) {
             const int kind = (j == 0) ? 5 : (j == k - 2) ? 4 : 6;
             if (!(tm & (1 << kind))) continue;
-            float3 cp[kMaxCross], cn[kMaxCross];
+            double3 cp[kMaxCross], cn[kMaxCross];
             const int nc = ghost_crossings(c, g, x[j].p, x[j + 1].p, cp, cn);
             for (int q = 0; q < nc; ++q) {
                 SF p{pD * pLi, 0};
                 if (kind == 4 || kind == 5) {
-                    const float3 o = (kind == 4) ? x[k - 1].p : x[0].p;
+                    const double3 o = d3((kind == 4) ? x[k - 1].p : x[0].p);
                     const Vtx &x1 = (kind == 4) ? x[k - 2] : x[1];
-                    const float3 w = unit3(x1.p - o);
-                    const float cg = fabsf(dot3(cn[q], w)), c1 = fabsf(dot3(x1.n, w));
-                    if (!(cg > 0.f)) continue;
-                    const float3 og = cp[q] - o, o1 = x1.p - o;
-                    p = sf_mul(p, dot3(og, og) / cg);
-                    p = sf_mul(p, c1 / dot3(o1, o1));
+                    const double3 o1 = dsub(d3(x1.p), o), w = dunit(o1);
+                    const double cg = fabs(ddot(cn[q], w)), c1 = fabs(ddot(d3(x1.n), w));
+                    if (!(cg > 0.0)) continue;
+                    const double3 og = dsub(cp[q], o);
+                    p = sf_mul_d(p, ddot(og, og) * c1 / (cg * ddot(o1, o1)));
                     if (kind == 4) {
                         for (int m = 1; m <= k - 3; ++m) p = sf_mul(p, pL[m]);
                     } else {
                         for (int m = 2; m <= k - 2; ++m) p = sf_mul(p, pE[m]);
                     }
                 } else {
-                    const float3 e = x[j + 1].p - x[j].p;
-                    const float3 w = unit3(e);
-                    const float cg = fabsf(dot3(cn[q], w));
-                    if (!(cg > 0.f)) continue;
-                    p = sf_mul(p, fabsf(dot3(x[j].n, w)) * fabsf(dot3(x[j + 1].n, w)) /
-                                      (cg * 4.0f * kPi));
-                    p = sf_mul(p, 1.0f / dot3(e, e));
+                    const double3 e = dsub(d3(x[j + 1].p), d3(x[j].p));
+                    const double3 w = dunit(e);
+                    const double cg = fabs(ddot(cn[q], w));
+                    if (!(cg > 0.0)) continue;
+                    p = sf_mul_d(p, fabs(ddot(d3(x[j].n), w)) * fabs(ddot(d3(x[j + 1].n), w)) /
+                                        (cg * 4.0 * kPi * ddot(e, e)));
                     for (int m = 1; m <= j - 1; ++m) p = sf_mul(p, pL[m]);
                     for (int m = j + 2; m <= k - 2; ++m) p = sf_mul(p, pE[m]);
                 }
@@ -1045,7 +1064,8 @@ enum {
     MAP_REJECT_NODYN = 2,
     MAP_REJECT_MULTI = 3,
     MAP_REJECT_INVERT = 4,
-    MAP_REJECT_JAC = 5
+    MAP_REJECT_JAC = 5,
+    MAP_OFF = 6                 // path mapping switched off
 };
 
 static __device__ bool reconnect_ok(const Ctx &c, int ga, const Vtx &a, int gap, const Vtx &ap, int gb,
@@ -1111,10 +1131,66 @@ static __device__ int map_step(Ctx &c, int g, int g2, const Vtx *x, Vtx *y, int 
     return MAP_ACCEPT;
 }
 
+// the first edge of a frame-g path is dynamic: x_1 lies on the object or the
+// camera ray to x_1 crosses the ghost (the object at its other-frame pose)
+static __device__ bool first_edge_dynamic(Ctx &c, int g, const Vtx *x, int k) {
+    if (k < 2 || !c.A.E.motion) return false;
+    if (is_dyn(c, x[1])) return true;
+    return !segment_clear(c, 3 - g, x[0], x[1], true);
+}
+
+// camera replay (Sec. 5, "Mapping between the dynamic and ghost pair": the
+// same camera direction in both frames): y_1 is the first hit of the camera
+// ray through x_1 in frame g2 (area Jacobian: ratio of the camera
+// densities), then the light side walks as for technique (2); the class of
+// paths with a dynamic first edge is closed under this map
+static __device__ void map_camera(Ctx &c, int g, int g2, const Vtx *x, int k, Vtx *y, MapInfo &mi) {
+    for (int j = 2; j <= k - 2; ++j)
+        if (is_dyn(c, x[j])) {
+            mi.status = MAP_REJECT_MULTI;
+            return;
+        }
+    const float3 w = unit3(x[1].p - x[0].p);
+    Vtx y1;
+    if (!trace_next(c, g2, y[0], w, y1) || dot3(y1.n, w) >= 0.f) {
+        mi.status = MAP_INVALID;
+        return;
+    }
+    y[1] = y1;
+    mi.replayed |= 2u;
+    const float px = pdf_camera_area(c.A.S, x[1]), py = pdf_camera_area(c.A.S, y[1]);
+    if (!(px > 0.f) || !(py > 0.f)) {
+        mi.status = MAP_INVALID;
+        return;
+    }
+    mi.J *= px / py;
+    for (int b = 2; b <= k - 2; ++b) {
+        const int st = map_step(c, g, g2, x, y, b - 1, b, b - 2, mi);
+        if (st != MAP_ACCEPT) {
+            mi.status = st;
+            return;
+        }
+    }
+    if (!first_edge_dynamic(c, g2, y, k)) {
+        mi.status = MAP_REJECT_INVERT;
+        return;
+    }
+    const float jm = c.A.S.jac_max;
+    if (!(mi.J <= jm && 1.0f / mi.J <= jm)) {
+        mi.status = MAP_REJECT_JAC;
+        return;
+    }
+    mi.status = MAP_ACCEPT;
+}
+
 static __device__ void map_path(Ctx &c, int g, int g2, const Vtx *x, int k, Vtx *y, MapInfo &mi) {
     mi.J = 1.0f;
     mi.replayed = 0u;
     for (int j = 0; j < k; ++j) y[j] = x[j];
+    if (c.A.map_mode == 2 && first_edge_dynamic(c, g, x, k)) {
+        map_camera(c, g, g2, x, k, y, mi);
+        return;
+    }
     int nd = 0, i = -1;
     for (int j = 1; j <= k - 2; ++j)
         if (is_dyn(c, x[j])) {
@@ -1156,6 +1232,12 @@ static __device__ void map_path(Ctx &c, int g, int g2, const Vtx *x, int k, Vtx 
     const float jm = c.A.S.jac_max;
     if (!(mi.J <= jm && 1.0f / mi.J <= jm)) {
         mi.status = MAP_REJECT_JAC;
+        return;
+    }
+    // the image must stay outside the camera-replay class (else the inverse
+    // map would differ)
+    if (c.A.map_mode == 2 && first_edge_dynamic(c, g2, y, k)) {
+        mi.status = MAP_REJECT_INVERT;
         return;
     }
     mi.status = MAP_ACCEPT;
@@ -1261,6 +1343,8 @@ static __device__ void evaluate_path(Ctx &c, PathCounts &pc, int g, const Vtx *x
     if (!c.A.E.motion) {
         for (int j = 0; j < n; ++j) y[j] = x[j];
         mi.status = MAP_ACCEPT;
+    } else if (c.A.map_mode == 0) {
+        mi.status = MAP_OFF;     // each frame estimates its own paths
     } else {
         map_path(c, g, g2, x, n, y, mi);
     }

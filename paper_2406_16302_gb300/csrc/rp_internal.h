@@ -133,6 +133,8 @@ struct LaunchArgs {
     unsigned long long *stats;  // ST_COUNT counters or null
     WaveBuf W;                  // wavefront buffers (wavefront mode)
     int residual;               // 1: residual techniques, 0: primal path tracing
+    int map_mode;               // 2: camera replay for dynamic first edges, else object
+                                // transform (default); 1: object transform only; 0: off
     KernelTimer *timer;         // host only: per-kernel event timing, or null
     GuideLaunch G;              // learned proposal (G.on = 0: none)
 };

@@ -84,7 +84,7 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
            "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_loss_grad",
            "rp_guide_train_step", "rp_guide_status", "rp_scene_set_guide",
            "rp_batch_create", "rp_batch_destroy", "rp_batch_launch", "rp_batch_set_seeds",
-           "rp_batch_info", "rp_batch_autotune",
+           "rp_batch_info", "rp_batch_autotune", "rp_scene_set_mapping",
            "rp_last_error"]
 
 GUIDE_WEIGHTS, GUIDE_IN, GUIDE_OUT = 20480, 80, 48
@@ -136,6 +136,7 @@ def lib():
         "rp_batch_set_seeds": (I, [P, P, P]),
         "rp_batch_info": (I, [P, P, P]),
         "rp_batch_autotune": (I, [P, P, U32, U32, P, P]),
+        "rp_scene_set_mapping": (I, [P, I]),
         "rp_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -399,6 +400,16 @@ def rp_guide_train_step(guide: Guide, lr=2e-3, stream=None):
 
 def rp_guide_status(guide: Guide):
     _check(lib().rp_guide_status(guide.h))
+
+
+RP_MAPPING_OFF, RP_MAPPING_OBJECT, RP_MAPPING_CAMERA = 0, 1, 2
+
+
+def rp_scene_set_mapping(scene: Scene, mode=RP_MAPPING_CAMERA):
+    """Path mapping mode (True means the default camera mode, False off)."""
+    if mode is True:
+        mode = RP_MAPPING_CAMERA
+    _check(lib().rp_scene_set_mapping(scene.h, int(mode)))
 
 
 def rp_scene_set_guide(scene: Scene, guide):

@@ -139,6 +139,10 @@ def _job(args):
         return o.render_primal(1, spp, seed)
     if kind == "p2":
         return o.render_primal(2, spp, seed)
+    if kind == "res_nomap":
+        o.set_mapping(0)
+    if kind == "res_objmap":
+        o.set_mapping(1)
     return o.render_residual(spp, seed, tech_mask=mask)
 
 

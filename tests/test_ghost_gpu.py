@@ -72,3 +72,43 @@ def test_ghost_techniques_need_motion(rp):
     ed = rp.Edit(sc, edit)
     img = rp.render_residual(sc, ed, 4, 1, tech_mask=rp.RP_TECH_GHOSTS).cpu().numpy()
     assert np.all(img == 0.0)
+
+
+def test_without_path_mapping_matches_oracle(rp):
+    scene, edit = S.cfg1_box_sphere(width=24, height=24, max_depth=5)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    rp.rp_scene_set_mapping(sc, False)
+    ora = O.Oracle(scene, edit)
+    ora.set_mapping(False)
+    N = sc.n_roots(4)
+    tally = Tally()
+    for tech in (1, 3, 5, 7):
+        for frame in (1, 2):
+            gpu = rp.dump_samples(sc, ed, tech, frame, 4, 5, 0, N, tech_mask=127)
+            ref = ora.dump(tech, frame, 4, 5, 0, N, tech_mask=127)
+            assert np.all(gpu["vb"] == 0.0)
+            frac, n, bad = _compare(gpu, ref)
+            tally.add(frac, n, bad, ("no mapping", tech, frame))
+    tally.check()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_mapping_modes_match_oracle(rp, mode):
+    """Object-transform mapping for every path (1) and the default camera
+    mapping for dynamic first edges (2), per sample against the oracle."""
+    scene, edit = S.cfg1_box_sphere(width=32, height=32, max_depth=6)
+    sc = rp.Scene(scene)
+    ed = rp.Edit(sc, edit)
+    rp.rp_scene_set_mapping(sc, mode)
+    ora = O.Oracle(scene, edit)
+    ora.set_mapping(mode)
+    N = sc.n_roots(4)
+    tally = Tally()
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            gpu = rp.dump_samples(sc, ed, tech, frame, 4, 9, 0, N)
+            ref = ora.dump(tech, frame, 4, 9, 0, N)
+            frac, n, bad = _compare(gpu, ref)
+            tally.add(frac, n, bad, (mode, tech, frame))
+    tally.check()

@@ -39,3 +39,27 @@ def test_ghost_techniques_need_motion():
     assert np.all(o.render_residual(8, 1, tech_mask=oracle.MASK_GHOSTS) == 0.0)
     for tech in (4, 5, 6):
         assert len(o.dump(tech, 2, 8, 1, 0, o.n_roots(8), tech_mask=127)) == 0
+
+
+@pytest.mark.parametrize("mask", [15, 127])
+def test_without_path_mapping_the_estimator_stays_unbiased(mask):
+    """Path mapping off: each frame's dynamic paths come from that frame's
+    sampling alone; the residual still agrees with correlated path tracing."""
+    K = 24
+    corr = H.run_many("corr", "cfg1_box_sphere", KW, range(1000, 1000 + K), 1024)
+    res = H.run_many("res_nomap", "cfg1_box_sphere", KW, range(11000, 11000 + K), 128, mask=mask)
+    z, zs = H.zscores(res, corr)
+    assert abs(zs) < 4.0, zs
+    assert np.sqrt((z ** 2).mean()) < 1.4
+
+
+def test_object_transform_mapping_stays_unbiased():
+    """Mapping mode 1 (the object transform for every path) against correlated
+    path tracing (mode 2, the default, is covered by the other residual pins)."""
+    import multiprocessing as mp
+    K = 24
+    corr = H.run_many("corr", "cfg1_box_sphere", KW, range(1000, 1000 + K), 1024)
+    res = H.run_many("res_objmap", "cfg1_box_sphere", KW, range(12000, 12000 + K), 128, mask=15)
+    z, zs = H.zscores(res, corr)
+    assert abs(zs) < 4.0, zs
+    assert np.sqrt((z ** 2).mean()) < 1.4
