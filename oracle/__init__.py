@@ -58,6 +58,8 @@ def lib():
                                     P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                     C.c_double]
         L.oracle_set_edit.argtypes = [P, P, P, P, P]
+        L.oracle_set_edit_multi.restype = C.c_int
+        L.oracle_set_edit_multi.argtypes = [P, C.c_int, P, P, P, P, P]
         L.oracle_set_brute_force.argtypes = [P, C.c_int]
         L.oracle_set_mapping.argtypes = [P, C.c_int]
         L.oracle_destroy.argtypes = [P]
@@ -219,6 +221,21 @@ class Oracle:
             self.set_edit(edit)
 
     def set_edit(self, edit):
+        """One edit of the whole dynamic mesh, or a list of edits of the
+        instances of a several-object dynamic mesh (scene.dyn_instance)."""
+        if isinstance(edit, (list, tuple)):
+            inst = getattr(self.scene, "dyn_instance", None)
+            if inst is None:
+                inst = np.zeros(self.scene.n_dyn, np.int32)
+            inst = np.ascontiguousarray(inst, dtype=np.int32)
+            assert len(inst) == self.scene.n_dyn and int(inst.max()) < len(edit)
+            arrs = [np.ascontiguousarray(np.stack([getattr(e, f) for e in edit]),
+                                         dtype=np.float32).ravel()
+                    for f in ("M1", "M2", "mat1", "mat2")]
+            self._edit = arrs + [inst]
+            r = lib().oracle_set_edit_multi(self.h, len(edit), _p(inst), *[_p(a) for a in arrs])
+            assert r == 0, "bad several-object edit"
+            return
         arrs = [np.ascontiguousarray(a, dtype=np.float32).ravel()
                 for a in (edit.M1, edit.M2, edit.mat1, edit.mat2)]
         self._edit = arrs

@@ -158,6 +158,8 @@ typedef struct {
     int id_offset;       /* global id = id_offset + local id */
 } bvh;
 
+#define MAX_INST 8
+
 typedef struct {
     /* static geometry (world) and dynamic object (object space) */
     int n_static, n_dyn;
@@ -166,11 +168,16 @@ typedef struct {
     tri *dyn_obj;        /* object-space dynamic triangles */
     material *mats;
     int n_mats;
-    /* per-frame world copies of the dynamic object, index 1 and 2 */
+    /* per-frame world copies of the dynamic object, index 1 and 2.  The
+     * dynamic mesh may be several objects moved together (an edit of several
+     * objects, Sec. 6): triangle i belongs to instance dyn_inst[i], which has
+     * its own transforms and materials */
     tri *dyn_world[3];
-    double M[3][12];
-    material dyn_mat[3];
-    int motion;          /* M1 != M2 */
+    int n_inst;
+    int *dyn_inst;       /* [n_dyn] instance of each dynamic triangle */
+    double M[3][MAX_INST][12];
+    material dyn_mat[3][MAX_INST];
+    int motion;          /* some instance has M1 != M2 */
     int has_edit;
     /* acceleration */
     bvh stat_bvh;
@@ -407,7 +414,8 @@ static const tri *prim_tri(const oscene *s, int g, int prim) {
 }
 
 static const material *prim_mat(const oscene *s, int g, int prim) {
-    return prim < s->n_static ? &s->mats[s->stat_mat[prim]] : &s->dyn_mat[g];
+    return prim < s->n_static ? &s->mats[s->stat_mat[prim]]
+                              : &s->dyn_mat[g][s->dyn_inst[prim - s->n_static]];
 }
 
 /* the surface point with barycentrics (b1, b2) on prim, in frame g */
@@ -1359,6 +1367,7 @@ static vec3 lin_MT(const double *M, vec3 a) {
 static vec3 guided_direction(const oscene *s, int g, const vtx *xD, rnd4 r, double *ratio) {
     const oguide *gd = s->guide;
     const tri *t = &s->dyn_obj[xD->prim - s->n_static];
+    const double *M = s->M[g][s->dyn_inst[xD->prim - s->n_static]];
     double b0 = 1.0 - xD->b1 - xD->b2;
     vec3 p_obj = add(add(scale(t->v0, b0), scale(t->v1, xD->b1)), scale(t->v2, xD->b2));
     vec3 nd = tri_normal(t);
@@ -1373,7 +1382,7 @@ static vec3 guided_direction(const oscene *s, int g, const vtx *xD, rnd4 r, doub
     vec3 w, wl;
     if (r.u[2] < 0.5) {
         w = cosine_dir(xD->n, r.u[0], r.u[1]);
-        wl = lin_MT(s->M[g], w);
+        wl = lin_MT(M, w);
     } else {
         double v = 2.0 * r.u[2] - 1.0, acc = 0.0;
         int j = G_LOBES - 1;
@@ -1382,7 +1391,7 @@ static vec3 guided_direction(const oscene *s, int g, const vtx *xD, rnd4 r, doub
             if (v < acc) { j = i; break; }
         }
         wl = vmf_sample(mu[j], kappa[j], r.u[0], r.u[1]);
-        w = lin_M(s->M[g], wl);
+        w = lin_M(M, wl);
     }
     double pc = cosine_pdf(xD->n, w), pv = 0.0;
     for (int j = 0; j < G_LOBES; ++j) pv += pi[j] * vmf_pdf(mu[j], kappa[j], wl);
@@ -1746,27 +1755,52 @@ void *oracle_create(const float *sv, int n_sv, const uint32_t *st, const uint32_
     return s;
 }
 
-int oracle_set_edit(void *h, const float *M1, const float *M2, const float *mat1,
-                    const float *mat2) {
+/* an edit of n objects moved (or re-materialed) together: dynamic triangle i
+ * belongs to instance inst[i] (0..n-1), whose object-to-world transforms in
+ * frames 1 and 2 are M1[12 k..], M2[12 k..] and whose materials are
+ * mat1[12 k..], mat2[12 k..] */
+int oracle_set_edit_multi(void *h, int n, const int *inst, const float *M1, const float *M2,
+                          const float *mat1, const float *mat2) {
     oscene *s = (oscene *)h;
+    if (n < 1 || n > MAX_INST) return -1;
+    for (int i = 0; i < s->n_dyn; ++i)
+        if (inst[i] < 0 || inst[i] >= n) return -1;
+    s->n_inst = n;
+    free(s->dyn_inst);
+    s->dyn_inst = (int *)malloc(sizeof(int) * (size_t)(s->n_dyn > 0 ? s->n_dyn : 1));
+    for (int i = 0; i < s->n_dyn; ++i) s->dyn_inst[i] = inst[i];
+    s->motion = 0;
     for (int f = 1; f <= 2; ++f) {
         const float *M = (f == 1) ? M1 : M2;
-        for (int i = 0; i < 12; ++i) s->M[f][i] = M[i];
-        s->dyn_mat[f] = read_material((f == 1) ? mat1 : mat2);
+        const float *m = (f == 1) ? mat1 : mat2;
+        for (int k = 0; k < n; ++k) {
+            for (int i = 0; i < 12; ++i) s->M[f][k][i] = M[12 * k + i];
+            s->dyn_mat[f][k] = read_material(m + 12 * k);
+        }
         if (s->has_edit) { free(s->dyn_world[f]); bvh_free(&s->dyn_bvh[f]); }
         s->dyn_world[f] = (tri *)malloc(sizeof(tri) * (size_t)(s->n_dyn > 0 ? s->n_dyn : 1));
         for (int i = 0; i < s->n_dyn; ++i) {
-            s->dyn_world[f][i].v0 = apply_M(s->M[f], s->dyn_obj[i].v0);
-            s->dyn_world[f][i].v1 = apply_M(s->M[f], s->dyn_obj[i].v1);
-            s->dyn_world[f][i].v2 = apply_M(s->M[f], s->dyn_obj[i].v2);
+            const double *Mk = s->M[f][inst[i]];
+            s->dyn_world[f][i].v0 = apply_M(Mk, s->dyn_obj[i].v0);
+            s->dyn_world[f][i].v1 = apply_M(Mk, s->dyn_obj[i].v1);
+            s->dyn_world[f][i].v2 = apply_M(Mk, s->dyn_obj[i].v2);
         }
         bvh_build(&s->dyn_bvh[f], s->dyn_world[f], s->n_dyn, s->n_static);
     }
-    s->motion = 0;
-    for (int i = 0; i < 12; ++i)
+    for (int i = 0; i < 12 * n; ++i)
         if (M1[i] != M2[i]) s->motion = 1;
     s->has_edit = 1;
     return 0;
+}
+
+/* an edit of the whole dynamic mesh as one object */
+int oracle_set_edit(void *h, const float *M1, const float *M2, const float *mat1,
+                    const float *mat2) {
+    oscene *s = (oscene *)h;
+    int *inst = (int *)calloc((size_t)(s->n_dyn > 0 ? s->n_dyn : 1), sizeof(int));
+    int r = oracle_set_edit_multi(h, 1, inst, M1, M2, mat1, mat2);
+    free(inst);
+    return r;
 }
 
 void oracle_set_brute_force(void *h, int on) { ((oscene *)h)->brute_force = on; }
@@ -1784,7 +1818,7 @@ void oracle_destroy(void *h) {
     if (s->has_edit)
         for (int f = 1; f <= 2; ++f) { free(s->dyn_world[f]); bvh_free(&s->dyn_bvh[f]); }
     free(s->stat); free(s->stat_mat); free(s->dyn_obj); free(s->mats);
-    free(s->dyn_cdf); free(s->emit_ids); free(s->emit_cdf);
+    free(s->dyn_cdf); free(s->emit_ids); free(s->emit_cdf); free(s->dyn_inst);
     free(s->guide);
     free(s);
 }

@@ -78,6 +78,8 @@ class Scene:
     name: str = ""
     object_ranges: np.ndarray = None # (K, 2) uint32: movable objects 1..K as (first, count)
                                      # ranges of the static triangles
+    dyn_instance: np.ndarray = None  # (Td,) int32: instance of each dynamic triangle when the
+                                     # dynamic mesh is several objects edited together
 
     @property
     def n_static(self) -> int:
@@ -364,6 +366,60 @@ def cfg1_box_sphere(width=64, height=64, max_depth=4):
     return scene, edit
 
 
+def box_objects(width=64, height=64, max_depth=4, n_objects=8, level=2, seed=2406):
+    """The cfg1 box with n_objects movable icospheres (level 2: 320
+    triangles each, radius 0.11-0.16, seeded Lambert albedo) spread over the
+    floor on a 4 x 2 grid, for edits that move several objects at once (the
+    paper's scenes with 1, 2, 4 and 8 moving objects, Sec. 6).  The scene's
+    own dynamic mesh is a small sphere that appears only in edits that name
+    object 0; the edits of `move_objects` move objects 1..k."""
+    rng = np.random.RandomState(seed)
+    mb = MeshBuilder(); mats = []
+    _box_room(mb, mats)
+    sv, st, sm = mb.arrays()
+    verts = [np.asarray(sv, np.float64)]
+    tris = [np.asarray(st, np.int64)]
+    mids = [np.asarray(sm, np.int64)]
+    nv, nt = len(sv), len(st)
+    ranges = []
+    grid = [(x, z) for z in (-0.45, 0.15) for x in (-0.6, -0.2, 0.2, 0.6)]
+    for k in range(n_objects):
+        v, t = icosphere(level)
+        r = rng.uniform(0.11, 0.16)
+        x, z = grid[k % len(grid)]
+        c = np.array([x, -1.0 + r + 0.02, z - 0.3 * (k // len(grid))])
+        m = len(mats)
+        mats.append(material(LAMBERT, tuple(rng.uniform(0.3, 0.9, size=3))))
+        verts.append(v * r + c)
+        tris.append(t + nv)
+        mids.append(np.full(len(t), m))
+        ranges.append((nt, len(t)))
+        nv += len(v)
+        nt += len(t)
+    dv, dt = icosphere(1)
+    return Scene(np.concatenate(verts).astype(np.float32), np.concatenate(tris).astype(np.uint32),
+                 np.concatenate(mids).astype(np.uint32), (dv * 0.1).astype(np.float32),
+                 dt.astype(np.uint32), np.stack(mats).astype(np.float32),
+                 _box_camera(width, height), max_depth, d_min=0.01 * 2.0 * math.sqrt(3.0),
+                 name=f"box_objects_{n_objects}", object_ranges=np.array(ranges, dtype=np.uint32))
+
+
+def move_objects(scene: Scene, k: int, displacement: float, seed=7):
+    """Edits moving objects 1..k of `scene` together, each translated by
+    `displacement` along a seeded horizontal direction (its material kept);
+    a list for rp_edit_multi / the oracle's several-object edit."""
+    rng = np.random.RandomState(seed)
+    edits = []
+    for j in range(1, k + 1):
+        first, _ = (int(c) for c in scene.object_ranges[j - 1])
+        m = np.asarray(scene.materials[int(scene.static_material[first])], np.float32)
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        t = displacement * np.array([math.cos(phi), 0.0, math.sin(phi)])
+        edits.append(Edit(translate((0.0, 0.0, 0.0)), translate(t), m.copy(), m.copy(),
+                          name=f"move_{j}_by_{displacement}", object=j))
+    return edits
+
+
 def displaced_icosphere(level, radius, amp, seed):
     v, t = icosphere(level)
     d = value_noise_3d(v, 4.0, seed)
@@ -608,6 +664,39 @@ def object_view(scene: Scene, k: int) -> Scene:
                  np.asarray(scene.static_vertices)[used], inv.reshape(-1, 3).astype(np.uint32),
                  scene.materials, scene.camera, scene.max_depth, scene.alpha_min, scene.d_min,
                  scene.jacobian_max, scene.name + f"_object{k}")
+
+
+def objects_view(scene: Scene, ks) -> Scene:
+    """The same geometry with several objects as one dynamic mesh: the
+    listed objects (0: the scene's dynamic mesh, k >= 1: movable object k),
+    in that order, each an instance with its own transforms; movable objects
+    are removed from the static triangles.  Only array slicing."""
+    ks = [int(k) for k in ks]
+    assert len(set(ks)) == len(ks) and len(ks) >= 1
+    tri = np.asarray(scene.static_triangles)
+    keep = np.ones(len(tri), dtype=bool)
+    verts, tris, inst = [], [], []
+    nv = 0
+    for i, k in enumerate(ks):
+        if k == 0:
+            v = np.asarray(scene.dyn_vertices, np.float32)
+            t = np.asarray(scene.dyn_triangles, np.int64)
+        else:
+            first, count = (int(c) for c in scene.object_ranges[k - 1])
+            keep[first:first + count] = False
+            ot = tri[first:first + count]
+            used, inv = np.unique(ot.ravel(), return_inverse=True)
+            v = np.asarray(scene.static_vertices, np.float32)[used]
+            t = inv.reshape(-1, 3).astype(np.int64)
+        verts.append(v)
+        tris.append(t + nv)
+        inst.append(np.full(len(t), i, np.int32))
+        nv += len(v)
+    return Scene(scene.static_vertices, tri[keep], np.asarray(scene.static_material)[keep],
+                 np.concatenate(verts), np.concatenate(tris).astype(np.uint32),
+                 scene.materials, scene.camera, scene.max_depth, scene.alpha_min, scene.d_min,
+                 scene.jacobian_max, scene.name + "_objects" + "_".join(map(str, ks)),
+                 dyn_instance=np.concatenate(inst))
 
 
 def uv_sphere_fast(n_seg: int, n_ring: int):

@@ -126,7 +126,14 @@ def _job(args):
     import oracle
     from paper_2406_16302_gb300 import scenes
     kind, builder, bargs, seed, spp, mask, edit_kind, guide = args
-    scene, edit = getattr(scenes, builder)(**bargs)
+    if isinstance(edit_kind, tuple) and edit_kind[0] == "objects":
+        # objects 1..k of a several-object scene moved by d (one dynamic set)
+        _, k, d = edit_kind
+        full = getattr(scenes, builder)(**bargs)
+        edit = scenes.move_objects(full, k, d)
+        scene = scenes.objects_view(full, [e.object for e in edit])
+    else:
+        scene, edit = getattr(scenes, builder)(**bargs)
     if edit_kind == "identity":
         edit = scenes.identity_edit(edit)
     o = oracle.Oracle(scene, edit)
