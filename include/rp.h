@@ -132,6 +132,22 @@ typedef struct {
 } rp_edit_desc;
 
 rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out);
+
+/* An edit of n objects at once (1 <= n <= 8; Sec. 6 measures scenes with
+ * several moving objects): descs[k] names object k of the edit (distinct
+ * objects) with its transforms and materials, as for rp_edit.  The objects
+ * form one dynamic set: x_D is sampled by area over all of them (p = 1 /
+ * total area), a path with more than one dynamic vertex is rejected by the
+ * mapping (R4) whichever objects they lie on, and the ghost is every object
+ * at its other-frame pose.  The edit owns device tables (the area CDF over
+ * the objects, and a bit mask of the moved base poses when they are not one
+ * contiguous range of static triangles): keep it alive while any render or
+ * batch that uses it may run.  Errors: RP_ERR_INVALID_ARG (n out of range,
+ * an object listed twice or out of range, bad material), RP_ERR_UNSUPPORTED
+ * (non-rigid transform, emissive material), RP_ERR_OOM.  A scene with a
+ * learned proposal renders edits of one object only (RP_ERR_UNSUPPORTED). */
+rp_status rp_edit_multi(rp_scene *scene, const rp_edit_desc *descs, uint32_t n,
+                        rp_edit_handle **out);
 void rp_edit_destroy(rp_edit_handle *edit);
 
 /* Residual image I2 - I1 (Eq. shiftmapped restricted to dynamic paths,

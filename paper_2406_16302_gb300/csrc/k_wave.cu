@@ -55,7 +55,7 @@ __device__ __forceinline__ Vtx load_vtx(const Ctx &c, const WaveBuf &W, int slot
     v.b1 = W.b1[i];
     v.b2 = W.b2[i];
     v.prim = W.prim[i];
-    v.mat = v.prim < c.A.S.n_static ? (int)c.A.S.stat_mat[v.prim] : kMatDynamic;
+    v.mat = v.prim < c.A.S.n_static ? (int)c.A.S.stat_mat[v.prim] : kMatDynamic - inst_of(c.A.S, v.prim);
     return v;
 }
 
@@ -140,13 +140,14 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                 const bool live = D >= 4 && !vtx_black(c, g, xD);
                 if (A.G.on) {
                     // learned proposal: object-space x_D and normal for the
-                    // network's input and the training samples
+                    // network's input and the training samples (edits of one
+                    // object only)
                     const float4 ur = draw(lseed(A), root, T_3, g, SD_ROOT, 0);
                     const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
                     double b1, b2;
                     tri_sample(ur.y, ur.z, b1, b2);
-                    const float4 ta = A.S.dyn_tri[3 * q], tb = A.S.dyn_tri[3 * q + 1],
-                                 tcv = A.S.dyn_tri[3 * q + 2];
+                    const float4 *tq = A.S.inst[0].tri + 3 * q;
+                    const float4 ta = tq[0], tb = tq[1], tcv = tq[2];
                     const double3 v0 = d3(ta);
                     const double3 po = dadd(dadd(v0, dscale(dsub(d3(tb), v0), b1)),
                                             dscale(dsub(d3(tcv), v0), b2));
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                     if (A.G.on) {
                         const uint32_t slot = guide_slot(A.G, g, root);
                         if (slot != ~0u) {
-                            const double3 wl = dlinear_T(A.E.M[g], d3(w));
+                            const double3 wl = dlinear_T(A.E.M(0, g), d3(w));
                             const uint32_t C = A.G.smp.cap;
                             A.G.smp.w[slot] = (float)wl.x; A.G.smp.w[C + slot] = (float)wl.y;
                             A.G.smp.w[2 * C + slot] = (float)wl.z;
@@ -231,7 +232,8 @@ __global__ void __launch_bounds__(128) k_encode3(const __grid_constant__ LaunchA
         const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
         double b1, b2;
         tri_sample(ur.y, ur.z, b1, b2);
-        const float4 ta = A.S.dyn_tri[3 * q], tb = A.S.dyn_tri[3 * q + 1], tcv = A.S.dyn_tri[3 * q + 2];
+        const float4 *tq = A.S.inst[0].tri + 3 * q;
+        const float4 ta = tq[0], tb = tq[1], tcv = tq[2];
         const double3 v0 = d3(ta);
         const double3 po = dadd(dadd(v0, dscale(dsub(d3(tb), v0), b1)), dscale(dsub(d3(tcv), v0), b2));
         guide_encode_d(A.G.net.box, po, f3(ta.w, tb.w, tcv.w), A.G.gin + (size_t)r * kGIn);
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(256) k_start3g(const __grid_constant__ LaunchA
     const WaveBuf &W = A.W;
     Ctx c(A, nullptr);
     const int g = A.frame;
-    const float *M = A.E.M[g];
+    const float *M = A.E.M(0, g);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         if (!(W.flags[r] & RF_GUIDE)) continue;
         const uint32_t root = A.root_begin + r;

@@ -87,6 +87,8 @@ struct rp_guide_s {
 struct rp_scene_s {
     DevScene S{};
     std::vector<DevObject> objects;   // 0: the dynamic mesh; k >= 1: static triangle ranges
+    std::vector<std::vector<double>> obj_tri_area;   // per object: triangle areas (double)
+    std::vector<double> obj_area;     // per object: total area (double)
     double cam_hh = 0.0;              // tan(vfov / 2)
     std::vector<void *> allocs;
     int bvh_depth_static = 0, bvh_depth_dyn = 0;
@@ -134,6 +136,10 @@ struct rp_scene_s {
 
 struct rp_edit_s {
     DevEdit E{};
+    std::vector<void *> allocs;       // several objects: the area CDF and static skip bits
+    ~rp_edit_s() {
+        for (void *p : allocs) cudaFree(p);
+    }
 };
 
 extern "C" const char *rp_last_error(void) { return g_err.c_str(); }
@@ -296,13 +302,14 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
     dst = ptr;
     UP(bs.nodes, p4, S.stat.nodes);
     UP(bs.tris, p4, S.stat.tris);
-    UP(bd.nodes, p4, S.dyn.nodes);
-    UP(bd.tris, p4, S.dyn.tris);
+    DevObject o0{};
+    UP(bd.nodes, p4, o0.bvh.nodes);
+    UP(bd.tris, p4, o0.bvh.tris);
     UP(st, p4, S.stat_tri);
-    UP(dt, p4, S.dyn_tri);
+    UP(dt, p4, o0.tri);
     UP(smat, pu, S.stat_mat);
     UP(mats, pf, S.mats);
-    UP(dcdf, pu, S.dyn_cdf);
+    UP(dcdf, pu, o0.cdf);
     UP(ecdf, pu, S.emit_cdf);
     double2 *pd2;
     UP(cs_hi, pd2, S.cs_hi);
@@ -311,24 +318,21 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
 #undef UP
     S.stat.n_nodes = (int)(bs.nodes.size() / 4);
     S.stat.n_tris = ns;
-    S.dyn.n_nodes = (int)(bd.nodes.size() / 4);
-    S.dyn.n_tris = nd;
+    o0.bvh.n_nodes = (int)(bd.nodes.size() / 4);
+    o0.bvh.n_tris = nd;
     S.n_static = ns;
-    S.n_dyn = nd;
     S.n_emit = (int)eids.size();
     S.n_mats = (int)d->n_materials;
-    S.dyn_area = (float)dyn_area;
     S.emit_area = (float)acc;
     {
-        DevObject o0{};
-        o0.bvh = S.dyn;
-        o0.tri = S.dyn_tri;
-        o0.cdf = S.dyn_cdf;
         o0.n = nd;
-        o0.area = S.dyn_area;
+        o0.area = (float)dyn_area;
         o0.bs = bounding_sphere(dt);
-        S.dyn_bs = o0.bs;
         sc->objects.push_back(o0);
+        std::vector<double> ta(nd);
+        for (int i = 0; i < nd; ++i) ta[i] = area(&dt[3 * (size_t)i]);
+        sc->obj_tri_area.push_back(std::move(ta));
+        sc->obj_area.push_back(dyn_area);
     }
     // movable objects: a BVH in object space (their given coordinates), the
     // triangles by id and the area sampling table, as for the dynamic mesh
@@ -371,6 +375,10 @@ extern "C" rp_status rp_scene_create(const rp_scene_desc *d, rp_scene **out) {
         o.skip_lo = first;
         o.skip_n = count;
         sc->objects.push_back(o);
+        std::vector<double> ta(count);
+        for (int i = 0; i < count; ++i) ta[i] = area(&ot[3 * (size_t)i]);
+        sc->obj_tri_area.push_back(std::move(ta));
+        sc->obj_area.push_back(oa);
     }
     // camera basis in double, stored as float
     const float *c = d->camera;
@@ -448,40 +456,100 @@ static bool rigid(const float *M) {
     return det > 0.0;
 }
 
-static rp_status fill_edit(const rp_scene *sc, const rp_edit_desc *d, DevEdit &E) {
-    if (d->object >= sc->objects.size())
-        return fail(RP_ERR_INVALID_ARG, "edit object index out of range");
-    if (!rigid(d->M1) || !rigid(d->M2))
-        return fail(RP_ERR_UNSUPPORTED, "edit transforms must be rigid (rotation + translation)");
-    if (!material_ok(d->mat1) || !material_ok(d->mat2))
-        return fail(RP_ERR_INVALID_ARG, "invalid edit material");
-    for (int i = 8; i < 11; ++i)
-        if (d->mat1[i] != 0.f || d->mat2[i] != 0.f)
-            return fail(RP_ERR_UNSUPPORTED, "the edited object may not be emissive");
+// device tables of an edit of several objects (uploaded by rp_edit_multi)
+struct EditTables {
+    std::vector<uint32_t> cdf;        // area CDF thresholds over all objects' triangles
+    std::vector<uint32_t> skip_bits;  // static triangles of the moved base poses
+};
+
+// an edit of n objects (1 <= n <= kMaxInst); `tab` receives the tables that
+// several objects need (none for one object)
+static rp_status fill_edit_multi(const rp_scene *sc, const rp_edit_desc *d, uint32_t n, DevEdit &E,
+                                 EditTables *tab) {
+    if (n < 1 || n > (uint32_t)kMaxInst)
+        return fail(RP_ERR_INVALID_ARG, "an edit moves between 1 and 8 objects");
     std::memset(&E, 0, sizeof E);
-    std::memcpy(E.M[1], d->M1, sizeof(float) * 12);
-    std::memcpy(E.M[2], d->M2, sizeof(float) * 12);
-    invert_rigid(d->M1, E.Minv[1]);
-    invert_rigid(d->M2, E.Minv[2]);
-    std::memcpy(E.mat[1], d->mat1, sizeof(float) * 12);
-    std::memcpy(E.mat[2], d->mat2, sizeof(float) * 12);
-    E.motion = std::memcmp(d->M1, d->M2, sizeof(float) * 12) != 0;
-    E.object = (int)d->object;
-    E.skip_lo = sc->objects[d->object].skip_lo;
-    E.skip_n = sc->objects[d->object].skip_n;
+    E.n_inst = (int)n;
+    int lo = 0x7fffffff, hi = 0, covered = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const rp_edit_desc *e = d + k;
+        if (e->object >= sc->objects.size())
+            return fail(RP_ERR_INVALID_ARG, "edit object index out of range");
+        for (uint32_t j = 0; j < k; ++j)
+            if (d[j].object == e->object) return fail(RP_ERR_INVALID_ARG, "an object is edited twice");
+        if (!rigid(e->M1) || !rigid(e->M2))
+            return fail(RP_ERR_UNSUPPORTED, "edit transforms must be rigid (rotation + translation)");
+        if (!material_ok(e->mat1) || !material_ok(e->mat2))
+            return fail(RP_ERR_INVALID_ARG, "invalid edit material");
+        for (int i = 8; i < 11; ++i)
+            if (e->mat1[i] != 0.f || e->mat2[i] != 0.f)
+                return fail(RP_ERR_UNSUPPORTED, "the edited object may not be emissive");
+        std::memcpy(E.M_[k][0], e->M1, sizeof(float) * 12);
+        std::memcpy(E.M_[k][1], e->M2, sizeof(float) * 12);
+        invert_rigid(e->M1, E.Minv_[k][0]);
+        invert_rigid(e->M2, E.Minv_[k][1]);
+        std::memcpy(E.mat_[k][0], e->mat1, sizeof(float) * 12);
+        std::memcpy(E.mat_[k][1], e->mat2, sizeof(float) * 12);
+        if (std::memcmp(e->M1, e->M2, sizeof(float) * 12) != 0) E.motion = 1;
+        E.object[k] = (int)e->object;
+        const DevObject &o = sc->objects[e->object];
+        if (o.skip_n > 0) {
+            lo = std::min(lo, o.skip_lo);
+            hi = std::max(hi, o.skip_lo + o.skip_n);
+            covered += o.skip_n;
+        }
+    }
+    if (hi > 0) {
+        E.skip_lo = lo;
+        E.skip_n = hi - lo;
+        if (covered != hi - lo) {     // the base poses are not one contiguous range
+            if (!tab) return fail(RP_ERR_INVALID_ARG, "several-object edits need rp_edit_multi");
+            tab->skip_bits.assign(((size_t)(hi - lo) + 31) / 32, 0u);
+            for (uint32_t k = 0; k < n; ++k) {
+                const DevObject &o = sc->objects[d[k].object];
+                for (int i = o.skip_lo - lo; i < o.skip_lo - lo + o.skip_n && o.skip_n > 0; ++i)
+                    tab->skip_bits[(size_t)i >> 5] |= 1u << (i & 31);
+            }
+        }
+    }
+    if (n > 1) {
+        if (!tab) return fail(RP_ERR_INVALID_ARG, "several-object edits need rp_edit_multi");
+        // p(x_D) = 1 / (total area): thresholds of the CDF over the objects'
+        // triangles in edit order, as for one object
+        double tot = 0.0;
+        for (uint32_t k = 0; k < n; ++k) tot += sc->obj_area[d[k].object];
+        double acc = 0.0;
+        for (uint32_t k = 0; k < n; ++k)
+            for (double a : sc->obj_tri_area[d[k].object]) {
+                acc += a;
+                const double t = std::ceil(acc / tot * 16777216.0);
+                tab->cdf.push_back(t >= 16777216.0 ? 16777216u : (uint32_t)t);
+            }
+        tab->cdf.back() = 16777216u;
+    }
     return RP_OK;
 }
 
-// the scene as seen by an edit: its moved object in the dynamic slots
+static rp_status fill_edit(const rp_scene *sc, const rp_edit_desc *d, DevEdit &E) {
+    return fill_edit_multi(sc, d, 1, E, nullptr);
+}
+
+// the scene as seen by an edit: its objects as the dynamic set, their
+// dynamic triangle ids in edit order
 static DevScene scene_for_edit(const rp_scene *sc, const DevEdit &E) {
     DevScene S = sc->S;
-    const DevObject &o = sc->objects[E.object];
-    S.dyn = o.bvh;
-    S.dyn_tri = o.tri;
-    S.dyn_cdf = o.cdf;
-    S.n_dyn = o.n;
-    S.dyn_area = o.area;
-    S.dyn_bs = o.bs;
+    S.n_inst = E.n_inst;
+    int base = 0;
+    double area = 0.0;
+    for (int k = 0; k < E.n_inst; ++k) {
+        const DevObject &o = sc->objects[E.object[k]];
+        S.inst[k] = DevInst{o.bvh, o.tri, base, o.n, o.bs};
+        base += o.n;
+        area += sc->obj_area[E.object[k]];
+    }
+    S.n_dyn = base;
+    S.dyn_area = E.n_inst == 1 ? sc->objects[E.object[0]].area : (float)area;
+    S.dyn_cdf = E.n_inst == 1 ? sc->objects[E.object[0]].cdf : E.cdf;
     return S;
 }
 
@@ -498,11 +566,33 @@ static void set_resolution(const rp_scene *sc, DevScene &S, int W, int H) {
 }
 
 extern "C" rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out) {
-    if (!scene || !desc || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
+    return rp_edit_multi(scene, desc, 1, out);
+}
+
+extern "C" rp_status rp_edit_multi(rp_scene *scene, const rp_edit_desc *descs, uint32_t n,
+                                   rp_edit_handle **out) {
+    if (!scene || !descs || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     rp_edit_handle *e = new rp_edit_s();
-    rp_status s = fill_edit(scene, desc, e->E);
+    EditTables tab;
+    rp_status s = fill_edit_multi(scene, descs, n, e->E, &tab);
     if (s != RP_OK) {
+        delete e;
+        return s;
+    }
+    auto up = [&](const std::vector<uint32_t> &v, const uint32_t **dst) -> rp_status {
+        if (v.empty()) return RP_OK;
+        void *p = nullptr;
+        cudaError_t ce = cudaMalloc(&p, v.size() * sizeof(uint32_t));
+        if (ce == cudaErrorMemoryAllocation) return fail(RP_ERR_OOM, "edit table allocation failed");
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc edit table");
+        e->allocs.push_back(p);
+        ce = cudaMemcpy(p, v.data(), v.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) return cuda_fail(ce, "upload edit table");
+        *dst = (const uint32_t *)p;
+        return RP_OK;
+    };
+    if ((s = up(tab.cdf, &e->E.cdf)) != RP_OK || (s = up(tab.skip_bits, &e->E.skip_bits)) != RP_OK) {
         delete e;
         return s;
     }
@@ -642,8 +732,16 @@ static rp_status run_waves(rp_scene *sc, LaunchArgs a, int tech, uint32_t r0, ui
     return RP_OK;
 }
 
+// the learned proposal encodes x_D in the one edited object's space
+static rp_status guide_fits(const rp_scene *sc, const DevEdit &E) {
+    if (sc->guide && E.n_inst > 1)
+        return fail(RP_ERR_UNSUPPORTED, "the learned proposal needs an edit of one object");
+    return RP_OK;
+}
+
 static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
                              uint32_t mask, double *d_out, cudaStream_t st) {
+    if (rp_status s = guide_fits(sc, E)) return s;
     LaunchArgs a = base_args(sc, E, spp, seed, mask);
     a.img = d_out;
     a.residual = 1;
@@ -769,6 +867,7 @@ extern "C" rp_status rp_dump_samples(rp_scene *scene, const rp_edit_handle *edit
     if (tech < 1 || tech > 7)
         return fail(RP_ERR_INVALID_ARG, "tech must be in 1..7");
     if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
+    if (rp_status s = guide_fits(scene, edit->E)) return s;
     if (root_end < root_begin || root_end > spp * (uint32_t)(scene->S.W * scene->S.H))
         return fail(RP_ERR_INVALID_ARG, "root range out of bounds");
     static_assert(sizeof(rp_record) == sizeof(Record), "record layout");
@@ -1226,6 +1325,7 @@ rp_status check_items(rp_scene *sc, const rp_batch_item *items, uint32_t n) {
         if (it.spp == 0 || (uint64_t)it.spp * W * H > 0xffffffffull)
             return fail(RP_ERR_INVALID_ARG, "item spp must be positive and spp * width * height fit in 32 bits");
         if (it.tech_mask == 0 || (it.tech_mask & ~RP_TECH_SEVEN)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
+        if (rp_status s = guide_fits(sc, it.edit->E)) return s;
     }
     return RP_OK;
 }

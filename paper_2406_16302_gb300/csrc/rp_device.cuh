@@ -134,7 +134,7 @@ static __device__ __forceinline__ float4 draw(uint64_t seed, uint32_t root, int 
 // ---------------------------------------------------------------------------
 
 constexpr int kMatCamera = -1;
-constexpr int kMatDynamic = -2;
+constexpr int kMatDynamic = -2;      // object k of the edit's dynamic set: kMatDynamic - k
 
 struct Mat {
     int type;
@@ -458,12 +458,15 @@ static __device__ __forceinline__ float safe_rcp(float x) {
     return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x);
 }
 
-// closest (any = false) or first found (any = true) hit in one BVH
-// triangles with ids in [skip_lo, skip_lo + skip_n) are not there (the
-// moved object's base pose inside the static BVH)
+// closest (any = false) or first found (any = true) hit in one BVH; leaf
+// ids plus id_add are the global triangle ids.  Triangles with ids in
+// [skip_lo, skip_lo + skip_n) (and, if skip_bits is set, whose bit
+// id - skip_lo is set) are not there: the moved objects' base poses inside
+// the static BVH
 static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin, float &tmax, int ex0,
                          int ex1, bool any, Hit &h, int *stack, Counters &cnt,
-                         int *overflow, int skip_lo = 0, int skip_n = 0) {
+                         int *overflow, int id_add = 0, int skip_lo = 0, int skip_n = 0,
+                         const uint32_t *skip_bits = nullptr) {
     if (B.n_nodes == 0) return false;
     const WtRay w = wt_setup(d);
     const float3 id = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -490,8 +493,12 @@ static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin,
             for (int i = first; i < first + count; ++i) {
                 ++cnt.tris;
                 const float4 v0 = __ldg(&B.tris[3 * i + 0]);
-                const int gid = __float_as_int(v0.w);
-                if (gid == ex0 || gid == ex1 || (unsigned)(gid - skip_lo) < (unsigned)skip_n) continue;
+                const int gid = __float_as_int(v0.w) + id_add;
+                if (gid == ex0 || gid == ex1) continue;
+                if ((unsigned)(gid - skip_lo) < (unsigned)skip_n &&
+                    (!skip_bits ||
+                     ((__ldg(&skip_bits[(unsigned)(gid - skip_lo) >> 5]) >> ((gid - skip_lo) & 31)) & 1u)))
+                    continue;
                 const float4 v1 = __ldg(&B.tris[3 * i + 1]);
                 const float4 v2 = __ldg(&B.tris[3 * i + 2]);
                 float tt, bb1, bb2;
@@ -545,8 +552,22 @@ struct Ctx {
     __device__ Ctx(const LaunchArgs &a, int *s) : A(a), stack(s), cnt{0, 0, 0, 0}, overflow(0) {}
 };
 
+// the instance of a dynamic triangle id, and its object-space triangle
+static __device__ __forceinline__ int inst_of(const DevScene &S, int prim) {
+    const int l = prim - S.n_static;
+    int k = 0;
+#pragma unroll 1
+    while (k + 1 < S.n_inst && l >= S.inst[k + 1].base) ++k;
+    return k;
+}
+
+static __device__ __forceinline__ const float4 *dyn_tri_of(const DevScene &S, int prim, int &k) {
+    k = inst_of(S, prim);
+    return S.inst[k].tri + 3 * (prim - S.n_static - S.inst[k].base);
+}
+
 static __device__ __forceinline__ Mat get_mat(const Ctx &c, int frame, int mat) {
-    if (mat == kMatDynamic) return load_mat(c.A.E.mat[frame]);
+    if (mat <= kMatDynamic) return load_mat(c.A.E.mat(kMatDynamic - mat, frame));
     return load_mat(c.A.S.mats + 12 * mat);
 }
 
@@ -557,20 +578,22 @@ static __device__ void refine_hit(const Ctx &c, int g, float3 o, float3 d, Hit &
 #if !RP_REFINE_FP64
     {   // single precision: the point of the watertight barycentrics
         const bool dynp = h.prim >= S.n_static;
-        const float4 *tr = dynp ? S.dyn_tri + 3 * (h.prim - S.n_static) : S.stat_tri + 3 * h.prim;
+        int k = 0;
+        const float4 *tr = dynp ? dyn_tri_of(S, h.prim, k) : S.stat_tri + 3 * h.prim;
         const float3 v0 = xyz(tr[0]);
         float3 p = v0 + (xyz(tr[1]) - v0) * h.b1 + (xyz(tr[2]) - v0) * h.b2;
-        if (dynp) p = affine(c.A.E.M[g], p);
+        if (dynp) p = affine(c.A.E.M(k, g), p);
         h.p = p;
         return;
     }
 #endif
     const bool dyn = h.prim >= S.n_static;
-    const float4 *tri = dyn ? S.dyn_tri + 3 * (h.prim - S.n_static) : S.stat_tri + 3 * h.prim;
+    int k = 0;
+    const float4 *tri = dyn ? dyn_tri_of(S, h.prim, k) : S.stat_tri + 3 * h.prim;
     double3 od = d3(o), dd = d3(d);
     if (dyn) {
-        od = daffine(c.A.E.Minv[g], od);
-        dd = dlinear(c.A.E.Minv[g], dd);
+        od = daffine(c.A.E.Minv(k, g), od);
+        dd = dlinear(c.A.E.Minv(k, g), dd);
     }
     const double3 v0 = d3(tri[0]), e1 = dsub(d3(tri[1]), v0), e2 = dsub(d3(tri[2]), v0);
     const double3 pv = dcross(dd, e2);
@@ -585,32 +608,55 @@ static __device__ void refine_hit(const Ctx &c, int g, float3 o, float3 d, Hit &
     const double3 qv = dcross(sv, e1);
     const double v = ddot(dd, qv) * inv;
     double3 p = dadd(dadd(v0, dscale(e1, u)), dscale(e2, v));
-    if (dyn) p = daffine(c.A.E.M[g], p);
+    if (dyn) p = daffine(c.A.E.M(k, g), p);
     h.p = tof(p);
     h.b1 = (float)u;
     h.b2 = (float)v;
 }
 
-// query of the scene in frame g: static BVH and the dynamic BVH under M_g
+// the segment o + t d, t in [tmin, tmax], passes within the radius of the
+// bounding sphere bs (object space)
+static __device__ __forceinline__ bool near_sphere(float4 bs, float3 o, float3 d, float tmin,
+                                                   float tmax) {
+    const float3 co = f3(bs.x, bs.y, bs.z) - o;
+    const float tc = fminf(fmaxf(dot3(co, d), tmin), tmax);
+    const float3 q = co - d * tc;
+    return dot3(q, q) <= bs.w * bs.w;
+}
+
+// query of the scene in frame g: the static BVH, then each object of the
+// dynamic set under its frame-g transform (a segment that misses an
+// object's bounding sphere skips its BVH)
 static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin, float tmax, int ex0,
                             int ex1, bool any, bool dyn_only, Hit &h) {
     const DevScene &S = c.A.S;
     bool found = false;
     if (!dyn_only) {
         found = traverse(S.stat, o, d, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow,
-                         c.A.E.skip_lo, c.A.E.skip_n);
+                         0, c.A.E.skip_lo, c.A.E.skip_n, c.A.E.skip_bits);
         if (found && any) return true;
     }
-    if (S.n_dyn > 0) {
-        const float *Mi = c.A.E.Minv[g];
-        float3 oo = affine(Mi, o), dd = linear(Mi, d);
-        // a segment that misses the object's bounding sphere skips its BVH
-        const float3 co = f3(S.dyn_bs.x, S.dyn_bs.y, S.dyn_bs.z) - oo;
-        const float tc = fminf(fmaxf(dot3(co, dd), tmin), tmax);
-        const float3 q = co - dd * tc;
-        if (dot3(q, q) <= S.dyn_bs.w * S.dyn_bs.w &&
-            traverse(S.dyn, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow))
+    if (S.n_inst == 1) {
+        // one object (the common edit): constant indexes keep its BVH
+        // pointers and transform in the kernel's parameter bank
+        const float *Mi = c.A.E.Minv(0, g);
+        const float3 oo = affine(Mi, o), dd = linear(Mi, d);
+        if (near_sphere(S.inst[0].bs, oo, dd, tmin, tmax) &&
+            traverse(S.inst[0].bvh, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt,
+                     &c.overflow))
             found = true;
+    } else {
+        for (int k = 0; k < S.n_inst; ++k) {
+            const DevInst &I = S.inst[k];
+            const float *Mi = c.A.E.Minv(k, g);
+            const float3 oo = affine(Mi, o), dd = linear(Mi, d);
+            if (near_sphere(I.bs, oo, dd, tmin, tmax) &&
+                traverse(I.bvh, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow,
+                         I.base)) {
+                found = true;
+                if (any) return true;
+            }
+        }
     }
     if (found && !any) refine_hit(c, g, o, d, h);
     return found;
@@ -620,7 +666,7 @@ static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin
 // ghost crossings of an edge); returns the number found
 static __device__ int traverse_all(const DevBVH &B, float3 o, float3 d, float tmin, float tmax,
                                    float *ts, int *prims, int maxh, int *stack, Counters &cnt,
-                                   int *overflow) {
+                                   int *overflow, int id_add) {
     if (B.n_nodes == 0) return 0;
     const WtRay w = wt_setup(d);
     const float3 id = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -650,7 +696,7 @@ static __device__ int traverse_all(const DevBVH &B, float3 o, float3 d, float tm
                 float tmx = tmax, tt, bb1, bb2;
                 if (tri_hit(w, o, xyz(v0), xyz(v1), xyz(v2), tmin, tmx, tt, bb1, bb2) && n < maxh) {
                     ts[n] = tt;
-                    prims[n] = __float_as_int(v0.w);
+                    prims[n] = __float_as_int(v0.w) + id_add;
                     ++n;
                 }
             }
@@ -689,28 +735,29 @@ constexpr int kMaxCross = 8;        // ghost crossings kept per edge
 // edge are ill-conditioned in single precision.
 static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, double3 *cp, double3 *cn) {
     const DevScene &S = c.A.S;
-    if (!c.A.E.motion || S.n_dyn == 0) return 0;
+    if (!c.A.E.motion) return 0;
     const int go = 3 - g;
     const float3 e = b - a;
     const float dist = len3(e);
     const float3 d = e * (1.0f / dist);
     const float tmin = S.eps, tmax = dist - S.eps;
-    const float *Mi = c.A.E.Minv[go];
-    const float3 oo = affine(Mi, a), dd = linear(Mi, d);
-    const float3 co = f3(S.dyn_bs.x, S.dyn_bs.y, S.dyn_bs.z) - oo;
-    const float tc = fminf(fmaxf(dot3(co, dd), tmin), tmax);
-    const float3 q = co - dd * tc;
-    if (dot3(q, q) > S.dyn_bs.w * S.dyn_bs.w) return 0;
     float ts[kMaxCross];
     int prims[kMaxCross];
-    const int n = traverse_all(S.dyn, oo, dd, tmin, tmax, ts, prims, kMaxCross, c.stack, c.cnt,
-                               &c.overflow);
+    int n = 0;
+    for (int k = 0; k < S.n_inst && n < kMaxCross; ++k) {
+        const DevInst &I = S.inst[k];
+        const float *Mi = c.A.E.Minv(k, go);
+        const float3 oo = affine(Mi, a), dd = linear(Mi, d);
+        if (!near_sphere(I.bs, oo, dd, tmin, tmax)) continue;
+        n += traverse_all(I.bvh, oo, dd, tmin, tmax, ts + n, prims + n, kMaxCross - n, c.stack,
+                          c.cnt, &c.overflow, I.base);
+    }
     const double3 da = d3(a), dw = dunit(dsub(d3(b), da));
     for (int i = 0; i < n; ++i) {
-        const int q3 = 3 * (prims[i] - S.n_static);
-        const float *M = c.A.E.M[go];
-        const double3 v0 = daffine(M, d3(S.dyn_tri[q3])), v1 = daffine(M, d3(S.dyn_tri[q3 + 1])),
-                      v2 = daffine(M, d3(S.dyn_tri[q3 + 2]));
+        int k;
+        const float4 *tr = dyn_tri_of(S, prims[i], k);
+        const float *M = c.A.E.M(k, go);
+        const double3 v0 = daffine(M, d3(tr[0])), v1 = daffine(M, d3(tr[1])), v2 = daffine(M, d3(tr[2]));
         const double3 nn = dcross(dsub(v1, v0), dsub(v2, v0));
         const double den = ddot(nn, dw);
         const double t = den != 0.0 ? ddot(nn, dsub(v0, da)) / den : (double)ts[i];
@@ -727,7 +774,7 @@ static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, double3
 struct Vtx {
     float3 p, n;
     int prim;      // -1: the pinhole
-    int mat;       // material index, kMatDynamic, or kMatCamera
+    int mat;       // material index, kMatCamera, or kMatDynamic - k on object k of the edit
     float b1, b2;
 };
 
@@ -749,14 +796,15 @@ static __device__ Vtx make_vertex_d(const Ctx &c, int g, int prim, double b1, do
         v.n = f3(a.w, b.w, d.w);
         v.mat = (int)S.stat_mat[prim];
     } else {
-        const int q = prim - S.n_static;
-        const float4 a = S.dyn_tri[3 * q], b = S.dyn_tri[3 * q + 1], d = S.dyn_tri[3 * q + 2];
+        int k;
+        const float4 *tr = dyn_tri_of(S, prim, k);
+        const float4 a = tr[0], b = tr[1], d = tr[2];
         double3 v0 = d3(a);
         double3 po = dadd(dadd(v0, dscale(dsub(d3(b), v0), b1)), dscale(dsub(d3(d), v0), b2));
-        const float *M = c.A.E.M[g];
+        const float *M = c.A.E.M(k, g);
         v.p = tof(daffine(M, po));
         v.n = tof(dlinear(M, d3(a.w, b.w, d.w)));
-        v.mat = kMatDynamic;
+        v.mat = kMatDynamic - k;
     }
     v.prim = prim;
     v.b1 = (float)b1;
@@ -776,10 +824,10 @@ static __device__ Vtx make_vertex_at(const Ctx &c, int g, int prim, float b1, fl
         v.n = f3(S.stat_tri[3 * prim].w, S.stat_tri[3 * prim + 1].w, S.stat_tri[3 * prim + 2].w);
         v.mat = (int)S.stat_mat[prim];
     } else {
-        const int q = prim - S.n_static;
-        v.n = tof(dlinear(c.A.E.M[g], d3(S.dyn_tri[3 * q].w, S.dyn_tri[3 * q + 1].w,
-                                          S.dyn_tri[3 * q + 2].w)));
-        v.mat = kMatDynamic;
+        int k;
+        const float4 *tr = dyn_tri_of(S, prim, k);
+        v.n = tof(dlinear(c.A.E.M(k, g), d3(tr[0].w, tr[1].w, tr[2].w)));
+        v.mat = kMatDynamic - k;
     }
     v.p = p;
     v.prim = prim;

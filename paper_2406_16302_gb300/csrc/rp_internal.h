@@ -15,6 +15,7 @@ constexpr int kMaxVerts = kMaxDepth + 2;
 constexpr int kStackDepth = 40;        // traversal stack entries per thread
 constexpr int kBvhMaxDepth = 38;       // the builder never exceeds this depth
 constexpr int kBlock = 128;            // threads per block of the path kernels
+constexpr int kMaxInst = 8;            // objects moved together by one edit
 
 // BVH node: both children's boxes, 64 bytes.
 //   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
@@ -30,13 +31,25 @@ struct DevBVH {
     int n_tris;
 };
 
+// one object of an edit's dynamic set: its BVH in object space (leaf ids
+// n_static + local id), triangles by local id (object-space vertices, .w =
+// unit normal), bounding sphere (object space, radius inflated so that the
+// test is conservative).  Its dynamic triangle ids are n_static + base +
+// local id.
+struct DevInst {
+    DevBVH bvh;
+    const float4 *tri;
+    int base, n;
+    float4 bs;
+};
+
 struct DevScene {
-    DevBVH stat, dyn;
+    DevBVH stat;
     const float4 *stat_tri;     // [n_static][3] world vertices by triangle id; .w = unit normal
-    const float4 *dyn_tri;      // [n_dyn][3] object-space vertices by triangle id; .w = unit normal
     const uint32_t *stat_mat;   // [n_static] material index
     const float *mats;          // [n_mats][12]
-    const uint32_t *dyn_cdf;    // [n_dyn] area CDF thresholds of the dynamic object, see below
+    const uint32_t *dyn_cdf;    // [n_dyn] area CDF thresholds over the dynamic triangles of all
+                                // instances (in instance order), see below
     const uint32_t *emit_cdf;   // [n_emit] area CDF thresholds of the emitters
     // uniforms are k / 2^24; triangle i is picked for the smallest i with
     // k < cdf[i], where cdf[i] = ceil(CDF_i * 2^24) in double precision
@@ -44,8 +57,8 @@ struct DevScene {
     const int *emit_ids;        // [n_emit] static triangle ids
     int n_static, n_dyn, n_emit, n_mats;
     float dyn_area, emit_area;
-    float4 dyn_bs;              // bounding sphere of the dynamic object (object space; radius
-                                // inflated so that the test is conservative)
+    int n_inst;                 // objects in the dynamic set (1..kMaxInst)
+    DevInst inst[kMaxInst];
     float3 cam_pos, cam_fwd, cam_right, cam_up;
     float hw, hh, pix_area, film_area;
     int W, H;
@@ -53,15 +66,23 @@ struct DevScene {
     float alpha_min, d_min, jac_max, eps;
 };
 
-// Per-frame data of an edit; index 1 = original frame, 2 = edited frame.
+// An edit of up to kMaxInst objects; per object and frame (g = 1 original,
+// 2 edited) its transforms and material, read through M(o, g), Minv(o, g)
+// and mat(o, g).
 struct DevEdit {
-    float M[3][12];             // object -> world (row-major 3x4)
-    float Minv[3][12];          // world -> object
-    float mat[3][12];           // the dynamic object's material
-    int motion;                 // M1 != M2
-    int object;                 // the moved object (0: the scene's dynamic mesh)
-    int skip_lo, skip_n;        // static triangles [skip_lo, skip_lo + skip_n) are the moved
-                                // object's base pose: static traversal skips them
+    float M_[kMaxInst][2][12];      // object -> world (row-major 3x4)
+    float Minv_[kMaxInst][2][12];   // world -> object
+    float mat_[kMaxInst][2][12];    // the object's material
+    int n_inst;
+    int object[kMaxInst];       // the edited objects (0: the scene's dynamic mesh)
+    int motion;                 // some object has M1 != M2
+    int skip_lo, skip_n;        // static triangles [skip_lo, skip_lo + skip_n) hold the moved
+                                // objects' base poses: static traversal skips them
+    const uint32_t *skip_bits;  // if set, only ids whose bit (id - skip_lo) is set are skipped
+    const uint32_t *cdf;        // several objects: the area CDF over all of them (edit-owned)
+    __host__ __device__ __forceinline__ const float *M(int o, int g) const { return M_[o][g - 1]; }
+    __host__ __device__ __forceinline__ const float *Minv(int o, int g) const { return Minv_[o][g - 1]; }
+    __host__ __device__ __forceinline__ const float *mat(int o, int g) const { return mat_[o][g - 1]; }
 };
 
 // a movable object: its BVH in object space, triangles, area sampling table

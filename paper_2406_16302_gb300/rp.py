@@ -75,7 +75,7 @@ RECORD_DTYPE = np.dtype([
     ("status", "<i4"), ("Pg", "<f4"), ("Py", "<f4"), ("J", "<f4")])
 
 # every symbol the header declares
-EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_destroy",
+EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_multi", "rp_edit_destroy",
            "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_f32_noalloc",
            "rp_render_residual_host",
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
@@ -106,6 +106,7 @@ def lib():
         "rp_scene_create": (I, [P, P]),
         "rp_scene_destroy": (None, [P]),
         "rp_edit": (I, [P, P, P]),
+        "rp_edit_multi": (I, [P, P, C.c_uint32, P]),
         "rp_edit_destroy": (None, [P]),
         "rp_render_residual": (I, [P, P, U32, U64, U32, P, P]),
         "rp_render_residual_f32": (I, [P, P, U32, U64, U32, P, P]),
@@ -233,12 +234,18 @@ class Scene:
 
 
 class Edit:
-    """rp_edit / rp_edit_destroy around a scenes.Edit."""
+    """rp_edit / rp_edit_destroy around a scenes.Edit, or rp_edit_multi
+    around a list of them (one per edited object)."""
 
     def __init__(self, scene: Scene, edit):
-        self.desc = edit_desc(edit)
         h = C.c_void_p()
-        _check(lib().rp_edit(scene.h, C.byref(self.desc), C.byref(h)))
+        if isinstance(edit, (list, tuple)):
+            descs = (rp_edit_desc * len(edit))(*[edit_desc(e) for e in edit])
+            self.desc = descs
+            _check(lib().rp_edit_multi(scene.h, descs, len(edit), C.byref(h)))
+        else:
+            self.desc = edit_desc(edit)
+            _check(lib().rp_edit(scene.h, C.byref(self.desc), C.byref(h)))
         self.h = h
 
     def close(self):

@@ -404,13 +404,14 @@ def box_objects(width=64, height=64, max_depth=4, n_objects=8, level=2, seed=240
                  name=f"box_objects_{n_objects}", object_ranges=np.array(ranges, dtype=np.uint32))
 
 
-def move_objects(scene: Scene, k: int, displacement: float, seed=7):
-    """Edits moving objects 1..k of `scene` together, each translated by
-    `displacement` along a seeded horizontal direction (its material kept);
-    a list for rp_edit_multi / the oracle's several-object edit."""
+def move_objects(scene: Scene, k: int, displacement: float, seed=7, objects=None):
+    """Edits moving objects 1..k of `scene` (or the listed `objects`)
+    together, each translated by `displacement` along a seeded horizontal
+    direction (its material kept); a list for rp_edit_multi / the oracle's
+    several-object edit."""
     rng = np.random.RandomState(seed)
     edits = []
-    for j in range(1, k + 1):
+    for j in (objects if objects is not None else range(1, k + 1)):
         first, _ = (int(c) for c in scene.object_ranges[j - 1])
         m = np.asarray(scene.materials[int(scene.static_material[first])], np.float32)
         phi = rng.uniform(0.0, 2.0 * math.pi)
