@@ -73,6 +73,9 @@ def workload(name):
     if name == "box_sphere_motion_64":
         scene, edit = scenes.cfg1_box_sphere()
         return scene, edit, 16
+    if name == "box_sphere_motion_256":
+        scene, edit = scenes.cfg1_box_sphere(width=256, height=256, max_depth=6)
+        return scene, edit, 64
     if name == "terrain_motion_1024":
         scene, edit = scenes.cfg3_terrain()
         return scene, edit, 16
@@ -209,12 +212,14 @@ def run_batch(args):
 
 
 def run_sweep(args):
-    """Displacement sweep on the cfg1 box (the sphere translated by d along
-    x): equal-time residual MSE of the residual estimator with the camera
-    mapping (default), the object-transform mapping and without mapping, with
-    the four and with all seven techniques, of correlated
-    path tracing and of re-rendering frame 2, against a converged reference
-    (trend only; the paper's own table is on its scenes)."""
+    """Hard-case sweeps on the cfg1 box (trend only; the paper's own table is
+    on its scenes): `sweep_displacement` translates the sphere by d along x,
+    `sweep_objects` moves 1, 2, 4 or 8 small objects at once (each by 0.1 in
+    a seeded horizontal direction).  Per case: equal-time residual MSE of the
+    residual estimator with the camera mapping (default), the
+    object-transform mapping and without mapping, with the four and with all
+    seven techniques, and of correlated path tracing, against a converged
+    reference (all seven techniques at 16 x 64 spp)."""
     import torch
     from paper_2406_16302_gb300 import build, rp, scenes
     build.build()
@@ -230,12 +235,21 @@ def run_sweep(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    def cases():
+        if args.workload == "sweep_objects":
+            full = scenes.box_objects(width=128, height=128, max_depth=6)
+            for k in (1, 2, 4, 8):
+                yield {"moving_objects": k}, full, scenes.move_objects(full, k, 0.1)
+        else:
+            for d in (0.02, 0.05, 0.1, 0.2, 0.4):
+                scene, edit = scenes.cfg1_box_sphere(width=128, height=128, max_depth=6)
+                edit.M2 = edit.M1.copy()
+                edit.M2[0, 3] += d
+                yield {"displacement": d}, scene, edit
+
     spp, K, R = 16, 4, 16
     rows = []
-    for d in (0.02, 0.05, 0.1, 0.2, 0.4):
-        scene, edit = scenes.cfg1_box_sphere(width=128, height=128, max_depth=6)
-        edit.M2 = edit.M1.copy()
-        edit.M2[0, 3] += d
+    for key, scene, edit in cases():
         sc = rp.Scene(scene)
         ed = rp.Edit(sc, edit)
 
@@ -254,7 +268,7 @@ def run_sweep(args):
         for i in range(R):
             ref += residual(4 * spp, 800000 + i, 127)[0]
         ref /= R
-        row = {"displacement": d}
+        row = dict(key)
         budget = None
         for name, mask, mapping in (("camera_4", 15, 2), ("object_4", 15, 1), ("off_4", 15, 0),
                                     ("camera_7", 127, 2), ("object_7", 127, 1)):
@@ -276,9 +290,11 @@ def run_sweep(args):
         row["correlated_pt"] = {"spp": spp, "mse": float(np.mean(ms)), "ms": t,
                                 "mse_at_budget": float(np.mean(ms)) * t / budget}
         rows.append(row)
-    print(json.dumps({"experiment": "displacement_sweep", "scene": "cfg1_box_sphere 128x128, max depth 6",
-                      "spp": spp, "repeats": K, "reference": f"all seven techniques, {R} x {4 * spp} spp",
-                      "rows": rows}), flush=True)
+    desc = ("box_objects 128x128, max depth 6, objects moved by 0.1"
+            if args.workload == "sweep_objects" else "cfg1_box_sphere 128x128, max depth 6")
+    print(json.dumps({"experiment": args.workload, "scene": desc, "spp": spp, "repeats": K,
+                      "reference": f"all seven techniques, {R} x {4 * spp} spp", "rows": rows}),
+          flush=True)
 
 
 def equal_time_mse(rp, sc, ed, scene, spp, K=4, ref_renders=16, guide_iters=30, guide_lr=1e-2):
@@ -529,7 +545,7 @@ def main():
         return run_reference(args)
     if args.workload == "batch_32_edits":
         return run_batch(args)
-    if args.workload == "sweep_displacement":
+    if args.workload in ("sweep_displacement", "sweep_objects"):
         return run_sweep(args)
 
     import torch

@@ -10,13 +10,16 @@
 //   identity edits) the mapping is the identity and the path is evaluated and
 //   splatted here with no ray at all; with motion every non-static path
 //   becomes a mapping task.
-// Stage C (k_map):   one thread per mapping task: object transform,
-//   reconnection or random replay in the other frame, two-way MIS, splat.
+// Stage C (motion):  k_map_a, one thread per mapping task: object
+//   transform, camera replay, reconnection or random replay in the other
+//   frame, two-way MIS; the mapped path's edges that need a visibility test
+//   go to a queue traced by k_trace_vis, and k_map_b emits the pairs.
 //
 // The random numbers, walk termination rules and path enumeration are those
 // of the one-thread-per-root kernels (rp_device.cuh), so both modes produce
 // the same samples.
 #include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
 
 #include "chain_fast.cuh"
 #include "guide_device.cuh"
@@ -659,7 +662,136 @@ __global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ Launc
 
 // --- stage C ---------------------------------------------------------------
 
-__global__ void __launch_bounds__(kBlock) k_map(const __grid_constant__ LaunchArgs A) {
+namespace {
+
+// reserve `k` consecutive entries of a queue with one atomic per coalesced
+// group of threads; returns the first
+__device__ __forceinline__ uint32_t append_n(unsigned int *counter, uint32_t k) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    const uint32_t ex = cg::exclusive_scan(g, k);
+    const uint32_t tot = g.shfl(ex + k, g.size() - 1);
+    uint32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, tot);
+    return g.shfl(base, 0) + ex;
+}
+
+__device__ __forceinline__ void store3(float *a, uint32_t stride, uint32_t i, float3 v) {
+    a[i] = v.x;
+    a[stride + i] = v.y;
+    a[2 * stride + i] = v.z;
+}
+
+__device__ __forceinline__ float3 load3(const float *a, uint32_t stride, uint32_t i) {
+    return f3(a[i], a[stride + i], a[2 * stride + i]);
+}
+
+// Stage C1 for base path x (n vertices) of task ti: its value, the mapped
+// path in the other frame and both splats of the two-way estimator
+// (Eq. shiftmapped; R3).  A rejected or invalid pair emits the one-way
+// value now.  An accepted pair needs the mapped path's edges to be clear
+// (replayed edges are clear by construction, unchanged edges are tested
+// against the dynamic objects only): those rays are queued for k_trace_vis
+// and the task waits for k_map_b; when the queue is full they are traced
+// here.
+__device__ void map_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t ti, uint32_t root,
+                         int tech, int sa, int sb) {
+    const LaunchArgs &A = c.A;
+    const WaveBuf &W = A.W;
+    const int g = A.frame, g2 = 3 - g;
+    int pa, ex;
+    const float3 fx = path_throughput(c, g, x, n, pa, ex);
+    if (zero3(fx)) return;
+    ++pc.paths;
+    const float invN = A.invN;
+    const float sign = (g == 2) ? 1.0f : -1.0f;
+    const SF Pg = mis_denominator(c, g, x, n);
+    const float3 v1 = fx * ldexpf(sign * invN / Pg.m, ex - Pg.e);     // one-way value
+    Vtx y[kMaxVerts];
+    MapInfo mi;
+    mi.J = 1.0f;
+    mi.replayed = 0u;
+    if (A.map_mode == 0) mi.status = MAP_OFF;
+    else map_path(c, g, g2, x, n, y, mi);
+    int pb = -1, ey = 0;
+    float3 fy = f3(0, 0, 0);
+    SF Py{0.f, 0};
+    if (mi.status == MAP_ACCEPT) {
+        fy = path_throughput(c, g2, y, n, pb, ey);
+        if (!zero3(fy)) Py = mis_denominator(c, g2, y, n);
+        if (zero3(fy) || !(Py.m > 0.f)) mi.status = MAP_INVALID;
+    }
+    if (mi.status != MAP_ACCEPT) {
+        if (mi.status != MAP_INVALID) ++pc.rejected;
+        emit(c, root, tech, g, sa, sb, pa, v1, -1, f3(0, 0, 0), mi.status, sf_val(Pg), 0.f, 0.f);
+        return;
+    }
+    const SF den = sf_add(Pg, SF{Py.m * mi.J, Py.e});
+    const float3 va = fx * ldexpf(sign * invN / den.m, ex - den.e);
+    const float3 vb = fy * ldexpf(-sign * mi.J * invN / den.m, ey - den.e);
+    // the mapped path's edges that need a test: not the replayed ones (the
+    // end farther from the dynamic vertex was found by tracing the edge)
+    int last = -1;
+    for (int j = 1; j <= n - 2; ++j)
+        if (is_dyn(c, y[j])) last = j;
+    uint32_t need = 0u, dyn_only = 0u;
+    for (int j = 0; j + 1 < n; ++j) {
+        const int far = (j + 1 <= last) ? j : j + 1;
+        if (mi.replayed & (1u << far)) continue;
+        need |= 1u << j;
+        if (same3(x[j].p, y[j].p) && same3(x[j + 1].p, y[j + 1].p)) dyn_only |= 1u << j;
+    }
+    const uint32_t ne = (uint32_t)__popc(need);
+    uint32_t base = ne ? append_n(W.counts + cnt_vis(), ne) : 0u;
+    if (ne && base + ne > W.qv) {
+        // queue full: mark the reserved entries void and trace here
+        for (uint32_t i = base; i < W.qv && i < base + ne; ++i) W.v_task[i] = ~0u;
+        bool clear = true;
+        for (int j = 0; j + 1 < n && clear; ++j)
+            if (need & (1u << j)) clear = segment_clear(c, g2, y[j], y[j + 1], (dyn_only >> j) & 1u);
+        if (!clear) {
+            emit(c, root, tech, g, sa, sb, pa, v1, -1, f3(0, 0, 0), MAP_INVALID, sf_val(Pg), 0.f, 0.f);
+            return;
+        }
+        ++pc.accepted;
+        emit(c, root, tech, g, sa, sb, pa, va, pb, vb, MAP_ACCEPT, sf_val(Pg), sf_val(Py), mi.J);
+        return;
+    }
+    if (!ne) {
+        ++pc.accepted;
+        emit(c, root, tech, g, sa, sb, pa, va, pb, vb, MAP_ACCEPT, sf_val(Pg), sf_val(Py), mi.J);
+        return;
+    }
+    for (int j = 0; j + 1 < n; ++j) {
+        if (!(need & (1u << j))) continue;
+        const float3 e = y[j + 1].p - y[j].p;
+        const float dist = len3(e);
+        store3(W.v_o, W.qv, base, y[j].p);
+        store3(W.v_d, W.qv, base, e * (1.0f / dist));
+        W.v_tmax[base] = dist - A.S.eps;
+        W.v_ex0[base] = y[j].prim;
+        W.v_ex1[base] = y[j + 1].prim;
+        W.v_task[base] = ti | (((dyn_only >> j) & 1u) << 31);
+        ++base;
+    }
+    W.m_pix[ti] = pa;
+    W.m_pix[W.qt + ti] = pb;
+    store3(W.m_val, W.qt, ti, va);
+    store3(W.m_val + 3 * (size_t)W.qt, W.qt, ti, vb);
+    store3(W.m_val + 6 * (size_t)W.qt, W.qt, ti, v1);
+    if (A.rec) {
+        W.m_w[ti] = sf_val(Pg);
+        W.m_w[W.qt + ti] = sf_val(Py);
+        W.m_w[2 * W.qt + ti] = mi.J;
+    }
+    W.m_vis[ti] = 1u;
+    const uint32_t p = append(W.counts + cnt_pend());
+    W.pend[p] = ti;                   // p < qt: one entry per task at most
+}
+
+}  // namespace
+
+// stage C1: one thread per mapping task (map_task)
+__global__ void __launch_bounds__(kBlock) k_map_a(const __grid_constant__ LaunchArgs A) {
     __shared__ int s_stack[kStackDepth * kBlock];
     Ctx c(A, s_stack + threadIdx.x);
     PathCounts pc{0, 0, 0};
@@ -669,7 +801,7 @@ __global__ void __launch_bounds__(kBlock) k_map(const __grid_constant__ LaunchAr
         const int4 t = A.W.tasks[i];
         const int lay = (t.y == T_7 || t.y == T_5) ? T_PT : t.y;   // slot layout of the technique
         const int k = assemble(c, (uint32_t)t.x, lay, t.z, t.w, x);
-        evaluate_path(c, pc, A.frame, x, k, A.root_begin + (uint32_t)t.x, t.y, t.z, t.w, true, true);
+        map_task(c, pc, x, k, i, A.root_begin + (uint32_t)t.x, t.y, t.z, t.w);
     }
     if (A.stats) {
         add_stat(A.stats, ST_PATHS, pc.paths);
@@ -680,6 +812,59 @@ __global__ void __launch_bounds__(kBlock) k_map(const __grid_constant__ LaunchAr
         add_stat(A.stats, ST_ACCEPTED, pc.accepted);
         add_stat(A.stats, ST_REJECTED, pc.rejected);
     }
+}
+
+// stage C2: the queued edges of mapped paths, in the other frame; a blocked
+// edge makes its task's pair invalid
+__global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_trace_vis(const __grid_constant__ LaunchArgs A) {
+    __shared__ int s_stack[kStackDepth * kBlock];
+    Ctx c(A, s_stack + threadIdx.x);
+    const WaveBuf &W = A.W;
+    const uint32_t n = min(W.counts[cnt_vis()], W.qv);
+    const int g2 = 3 - A.frame;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t tv = W.v_task[i];
+        if (tv == ~0u) continue;
+        const uint32_t ti = tv & 0x7fffffffu;
+        if (!W.m_vis[ti]) continue;               // another edge already blocked
+        Hit h;
+        ++c.cnt.rays_shadow;
+        if (scene_trace(c, g2, load3(W.v_o, W.qv, i), load3(W.v_d, W.qv, i), A.S.eps, W.v_tmax[i],
+                        W.v_ex0[i], W.v_ex1[i], true, (tv >> 31) != 0u, h))
+            W.m_vis[ti] = 0u;
+    }
+    if (A.stats) {
+        add_stat(A.stats, ST_RAYS_SHADOW, c.cnt.rays_shadow);
+        add_stat(A.stats, ST_NODES, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS, c.cnt.tris);
+        add_stat(A.stats, ST_NODES_S, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS_S, c.cnt.tris);
+    }
+}
+
+// stage C3: the waiting tasks emit their two-way pair, or the one-way value
+// when an edge of the mapped path was blocked (an invalid image, R4)
+__global__ void __launch_bounds__(256) k_map_b(const __grid_constant__ LaunchArgs A) {
+    Ctx c(A, nullptr);
+    const WaveBuf &W = A.W;
+    const uint32_t n = min(W.counts[cnt_pend()], W.qt);
+    unsigned int accepted = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t ti = W.pend[i];
+        const int4 t = W.tasks[ti];
+        const uint32_t root = A.root_begin + (uint32_t)t.x;
+        const float Pg = A.rec ? W.m_w[ti] : 0.f;
+        if (W.m_vis[ti]) {
+            ++accepted;
+            emit(c, root, t.y, A.frame, t.z, t.w, W.m_pix[ti], load3(W.m_val, W.qt, ti),
+                 W.m_pix[W.qt + ti], load3(W.m_val + 3 * (size_t)W.qt, W.qt, ti), MAP_ACCEPT, Pg,
+                 A.rec ? W.m_w[W.qt + ti] : 0.f, A.rec ? W.m_w[2 * W.qt + ti] : 0.f);
+        } else {
+            emit(c, root, t.y, A.frame, t.z, t.w, W.m_pix[ti], load3(W.m_val + 6 * (size_t)W.qt, W.qt, ti),
+                 -1, f3(0, 0, 0), MAP_INVALID, Pg, 0.f, 0.f);
+        }
+    }
+    if (A.stats) add_stat(A.stats, ST_ACCEPTED, accepted);
 }
 
 // --- host: one wave --------------------------------------------------------
@@ -734,6 +919,13 @@ inline int grid_for(uint32_t n, int block, int cap) {
         if (a.timer) timer_end(a.timer, name, s, e0_, e1_);                         \
     } while (0)
 
+// stage C: map every task, trace the mapped paths' queued edges, emit
+void map_stage(const LaunchArgs &a, cudaStream_t s, int gQ) {
+    RP_LAUNCH("k_map_a", gQ, kBlock, k_map_a, a);
+    RP_LAUNCH("k_trace_vis", gQ, kBlock, k_trace_vis, a);
+    RP_LAUNCH("k_map_b", gQ, 256, k_map_b, a);
+}
+
 template <int T>
 cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
     const uint32_t n = a.root_end - a.root_begin;
@@ -771,11 +963,11 @@ cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
     if constexpr (T == T_4 || T == T_5 || T == T_6) {
         // ghost techniques exist only with motion: always mapped
         RP_LAUNCH("k_enum", gE, 128, k_enum<T>, a);
-        RP_LAUNCH("k_map", gQ, kBlock, k_map, a);
+        map_stage(a, s, gQ);
     } else {
         if (a.residual && a.E.motion) {
             RP_LAUNCH("k_enum", gE, 128, k_enum<T>, a);
-            RP_LAUNCH("k_map", gQ, kBlock, k_map, a);
+            map_stage(a, s, gQ);
         } else {
             RP_LAUNCH("k_eval", gE, 128, k_eval_fast<T>, a);
         }

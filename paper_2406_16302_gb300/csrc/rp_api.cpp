@@ -668,8 +668,9 @@ static rp_status alloc_wavebuf(WaveBuf &W, std::vector<void *> &allocs, uint32_t
     W.qa = 3 * R;
     const int t3 = (D - 3) * (D - 2) / 2;
     W.qt = tasks ? (uint32_t)std::min<uint64_t>((uint64_t)R * (uint64_t)std::max(D + 1, t3),
-                                                 0xffffffffull)
+                                                 0x7ffffffeull)
                  : 0u;
+    W.qv = tasks ? std::max(W.qa, W.qt) : 0u;
     auto free_all = [&]() {
         for (void *p : allocs) cudaFree(p);
         allocs.clear();
@@ -696,7 +697,13 @@ static rp_status alloc_wavebuf(WaveBuf &W, std::vector<void *> &allocs, uint32_t
     A_(W.h_p, W.qc * 12ull)
     A_(W.a_o, W.qa * 12ull) A_(W.a_d, W.qa * 12ull) A_(W.a_tmax, W.qa * 4ull)
     A_(W.a_ex0, W.qa * 4ull) A_(W.a_ex1, W.qa * 4ull) A_(W.a_tag, W.qa * 4ull)
-    if (tasks) { A_(W.tasks, W.qt * 16ull) }
+    if (tasks) {
+        A_(W.tasks, W.qt * 16ull)
+        A_(W.v_o, W.qv * 12ull) A_(W.v_d, W.qv * 12ull) A_(W.v_tmax, W.qv * 4ull)
+        A_(W.v_ex0, W.qv * 4ull) A_(W.v_ex1, W.qv * 4ull) A_(W.v_task, W.qv * 4ull)
+        A_(W.m_pix, W.qt * 8ull) A_(W.m_val, W.qt * 36ull) A_(W.m_w, W.qt * 12ull)
+        A_(W.m_vis, W.qt * 4ull) A_(W.pend, W.qt * 4ull)
+    }
     A_(W.counts, kCountSlots * 4ull)
 #undef A_
     return RP_OK;

@@ -61,13 +61,27 @@ struct WaveBuf {
     // mapping tasks: (root, technique, sa, sb)
     uint32_t qt;
     int4 *tasks;
-    // counters: closest [kMaxIter], shadow [kMaxIter], tasks [1]
+    // deferred visibility of mapped paths: the edges of accepted mapped
+    // paths that need a test, queued by k_map_a and traced by k_trace_vis;
+    // per task the splats k_map_b emits once the rays are traced
+    uint32_t qv;                   // ray capacity
+    float *v_o, *v_d, *v_tmax;     // v_o, v_d: [3][qv]
+    int *v_ex0, *v_ex1;
+    uint32_t *v_task;              // task index | 1 << 31 for a dynamic-only test; ~0u: none
+    int *m_pix;                    // [2][qt] pixel of the base path, of the mapped path
+    float *m_val;                  // [9][qt] two-way base splat, mapped splat, one-way splat
+    float *m_w;                    // [3][qt] P_g(x), P_g'(y), J (for records)
+    uint32_t *m_vis;               // [qt] 1 while none of the task's rays is blocked
+    uint32_t *pend;                // [qt] tasks waiting for their rays
+    // counters: closest [kMaxIter], shadow [kMaxIter], tasks, rays, pending
     unsigned int *counts;
 };
 
 __host__ __device__ __forceinline__ int cnt_closest(int it) { return it; }
 __host__ __device__ __forceinline__ int cnt_shadow(int it) { return kMaxIter + it; }
 __host__ __device__ __forceinline__ int cnt_tasks() { return 2 * kMaxIter; }
-constexpr int kCountSlots = 2 * kMaxIter + 1;
+__host__ __device__ __forceinline__ int cnt_vis() { return 2 * kMaxIter + 1; }
+__host__ __device__ __forceinline__ int cnt_pend() { return 2 * kMaxIter + 2; }
+constexpr int kCountSlots = 2 * kMaxIter + 3;
 
 }  // namespace rp
