@@ -704,7 +704,11 @@ __device__ void map_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t t
     ++pc.paths;
     const float invN = A.invN;
     const float sign = (g == 2) ? 1.0f : -1.0f;
-    const SF Pg = mis_denominator(c, g, x, n);
+    // the ghost terms of P_g(x) search x's edges against the objects at
+    // their frame-g' pose: the same query as the dynamic-only visibility of
+    // an edge the mapping leaves unchanged
+    uint32_t searched = 0u, crossed = 0u;
+    const SF Pg = mis_denominator(c, g, x, n, &searched, &crossed);
     const float3 v1 = fx * ldexpf(sign * invN / Pg.m, ex - Pg.e);     // one-way value
     Vtx y[kMaxVerts];
     MapInfo mi;
@@ -715,9 +719,19 @@ __device__ void map_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t t
     int pb = -1, ey = 0;
     float3 fy = f3(0, 0, 0);
     SF Py{0.f, 0};
+    uint32_t same = 0u;              // edges the mapping leaves unchanged
+    if (mi.status == MAP_ACCEPT) {
+        for (int j = 0; j + 1 < n; ++j)
+            if (same3(x[j].p, y[j].p) && same3(x[j + 1].p, y[j + 1].p)) same |= 1u << j;
+        // an unchanged edge that crosses the objects at their frame-g' pose
+        // blocks the mapped path
+        if (same & crossed) mi.status = MAP_INVALID;
+    }
     if (mi.status == MAP_ACCEPT) {
         fy = path_throughput(c, g2, y, n, pb, ey);
-        if (!zero3(fy)) Py = mis_denominator(c, g2, y, n);
+        // an unchanged edge of y crosses nothing at the frame-g pose: it is
+        // an edge of x, which is clear in frame g
+        if (!zero3(fy)) Py = mis_denominator(c, g2, y, n, nullptr, nullptr, same);
         if (zero3(fy) || !(Py.m > 0.f)) mi.status = MAP_INVALID;
     }
     if (mi.status != MAP_ACCEPT) {
@@ -737,8 +751,11 @@ __device__ void map_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t t
     for (int j = 0; j + 1 < n; ++j) {
         const int far = (j + 1 <= last) ? j : j + 1;
         if (mi.replayed & (1u << far)) continue;
+        if ((same >> j) & 1u) {
+            if ((searched >> j) & 1u) continue;       // already known clear (above)
+            dyn_only |= 1u << j;
+        }
         need |= 1u << j;
-        if (same3(x[j].p, y[j].p) && same3(x[j + 1].p, y[j + 1].p)) dyn_only |= 1u << j;
     }
     const uint32_t ne = (uint32_t)__popc(need);
     uint32_t base = ne ? append_n(W.counts + cnt_vis(), ne) : 0u;

@@ -458,6 +458,12 @@ static __device__ __forceinline__ float safe_rcp(float x) {
     return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x);
 }
 
+// The path-level routines below that trace rays or walk a whole path
+// (trace_next, segment_clear, ghost_crossings, path_throughput,
+// mis_denominator, map_step) are kept out of line: the mapping kernel calls
+// each from several places, and inlined copies of the traversal loop in
+// every caller overflow the instruction cache when its lanes diverge.
+
 // closest (any = false) or first found (any = true) hit in one BVH; leaf
 // ids plus id_add are the global triangle ids.  Triangles with ids in
 // [skip_lo, skip_lo + skip_n) (and, if skip_bits is set, whose bit
@@ -538,6 +544,15 @@ static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin,
         }
     }
     return found;
+}
+
+// one out-of-line copy of the traversal loop for the path-level routines
+static __device__ __noinline__ bool traverse_ol(const DevBVH &B, float3 o, float3 d, float tmin,
+                                                float &tmax, int ex0, int ex1, bool any, Hit &h,
+                                                int *stack, Counters &cnt, int *overflow, int id_add,
+                                                int skip_lo, int skip_n, const uint32_t *skip_bits) {
+    return traverse(B, o, d, tmin, tmax, ex0, ex1, any, h, stack, cnt, overflow, id_add, skip_lo,
+                    skip_n, skip_bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -662,6 +677,33 @@ static __device__ bool scene_trace(Ctx &c, int g, float3 o, float3 d, float tmin
     return found;
 }
 
+// scene_trace for the path-level routines: out of line, with one copy of
+// the traversal loop for the static BVH and every object
+static __device__ __noinline__ bool scene_trace_ol(Ctx &c, int g, float3 o, float3 d, float tmin,
+                                                   float tmax, int ex0, int ex1, bool any,
+                                                   bool dyn_only, Hit &h) {
+    const DevScene &S = c.A.S;
+    bool found = false;
+    if (!dyn_only) {
+        found = traverse_ol(S.stat, o, d, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow,
+                            0, c.A.E.skip_lo, c.A.E.skip_n, c.A.E.skip_bits);
+        if (found && any) return true;
+    }
+    for (int k = 0; k < S.n_inst; ++k) {
+        const DevInst &I = S.inst[k];
+        const float *Mi = c.A.E.Minv(k, g);
+        const float3 oo = affine(Mi, o), dd = linear(Mi, d);
+        if (near_sphere(I.bs, oo, dd, tmin, tmax) &&
+            traverse_ol(I.bvh, oo, dd, tmin, tmax, ex0, ex1, any, h, c.stack, c.cnt, &c.overflow,
+                        I.base, 0, 0, nullptr)) {
+            found = true;
+            if (any) return true;
+        }
+    }
+    if (found && !any) refine_hit(c, g, o, d, h);
+    return found;
+}
+
 // every hit of a ray with t in (tmin, tmax) in one BVH, up to maxh (the
 // ghost crossings of an edge); returns the number found
 static __device__ int traverse_all(const DevBVH &B, float3 o, float3 d, float tmin, float tmax,
@@ -733,7 +775,7 @@ constexpr int kMaxCross = 8;        // ghost crossings kept per edge
 // densities divide by |n . w|, and near the silhouette (where area sampling
 // of the ghost puts many samples) both that and the crossing's place on the
 // edge are ill-conditioned in single precision.
-static __device__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, double3 *cp, double3 *cn) {
+static __device__ __noinline__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, double3 *cp, double3 *cn) {
     const DevScene &S = c.A.S;
     if (!c.A.E.motion) return 0;
     const int go = 3 - g;
@@ -917,7 +959,7 @@ static __device__ __forceinline__ SF sf_add(SF a, SF b) {
 static __device__ __forceinline__ float sf_val(SF a) { return ldexpf(a.m, a.e); }
 
 // path throughput f(x) (Eq. pathcontribution) as f * 2^e
-static __device__ float3 path_throughput(const Ctx &c, int g, const Vtx *x, int k, int &pix, int &e) {
+static __device__ __noinline__ float3 path_throughput(const Ctx &c, int g, const Vtx *x, int k, int &pix, int &e) {
     const DevScene &S = c.A.S;
     e = 0;
     float cc;
@@ -988,7 +1030,14 @@ static __device__ float step_pdf(const Ctx &c, int g, const Vtx *x, int cond, in
 // the balance-heuristic denominator of a path: the sum over the enabled
 // techniques that can produce it of their area densities (Sec. 4.3), each a
 // product of single-precision factors kept as SF
-static __device__ SF mis_denominator(Ctx &c, int g, const Vtx *x, int k) {
+// The ghost terms search each edge j of the path for crossings with the
+// object at its other-frame pose: *searched gets bit j for every edge
+// searched and *crossed bit j when one was found; edges in known_clear are
+// not searched (they are known to cross nothing).
+static __device__ __noinline__ SF mis_denominator(Ctx &c, int g, const Vtx *x, int k,
+                                                  uint32_t *searched = nullptr,
+                                                  uint32_t *crossed = nullptr,
+                                                  uint32_t known_clear = 0u) {
     const DevScene &S = c.A.S;
     const int tm = c.A.tech_mask;
     const bool t1 = tm & 1, t2 = tm & 2, t3 = tm & 4, t7 = tm & 8;
@@ -1033,9 +1082,11 @@ static __device__ SF mis_denominator(Ctx &c, int g, const Vtx *x, int k) {
     if ((tm & 0x70) && c.A.E.motion && k >= 3) {
         for (int j = 0; j <= k - 2; ++j) {
             const int kind = (j == 0) ? 5 : (j == k - 2) ? 4 : 6;
-            if (!(tm & (1 << kind))) continue;
+            if (!(tm & (1 << kind)) || ((known_clear >> j) & 1u)) continue;
             double3 cp[kMaxCross], cn[kMaxCross];
             const int nc = ghost_crossings(c, g, x[j].p, x[j + 1].p, cp, cn);
+            if (searched) *searched |= 1u << j;
+            if (crossed && nc > 0) *crossed |= 1u << j;
             for (int q = 0; q < nc; ++q) {
                 SF p{pD * pLi, 0};
                 if (kind == 4 || kind == 5) {
@@ -1072,20 +1123,20 @@ static __device__ SF mis_denominator(Ctx &c, int g, const Vtx *x, int k) {
 // visibility
 // ---------------------------------------------------------------------------
 
-static __device__ bool segment_clear(Ctx &c, int g, const Vtx &a, const Vtx &b, bool dyn_only) {
+static __device__ __noinline__ bool segment_clear(Ctx &c, int g, const Vtx &a, const Vtx &b, bool dyn_only) {
     float3 e = b.p - a.p;
     float dist = len3(e);
     float3 d = e * (1.0f / dist);
     Hit h;
     ++c.cnt.rays_shadow;
-    return !scene_trace(c, g, a.p, d, c.A.S.eps, dist - c.A.S.eps, a.prim, b.prim, true, dyn_only,
+    return !scene_trace_ol(c, g, a.p, d, c.A.S.eps, dist - c.A.S.eps, a.prim, b.prim, true, dyn_only,
                         h);
 }
 
-static __device__ bool trace_next(Ctx &c, int g, const Vtx &a, float3 d, Vtx &out) {
+static __device__ __noinline__ bool trace_next(Ctx &c, int g, const Vtx &a, float3 d, Vtx &out) {
     Hit h;
     ++c.cnt.rays_closest;
-    if (!scene_trace(c, g, a.p, d, c.A.S.eps, __int_as_float(0x7f800000), a.prim, -1, false, false,
+    if (!scene_trace_ol(c, g, a.p, d, c.A.S.eps, __int_as_float(0x7f800000), a.prim, -1, false, false,
                      h))
         return false;
     out = make_vertex_at(c, g, h.prim, h.b1, h.b2, h.p);
@@ -1134,7 +1185,7 @@ struct MapInfo {
 
 // one walk step: x[b] was reached from x[a], sampled with conditioning x[cc]
 // (cc < 0: cosine step); fills y[b]
-static __device__ int map_step(Ctx &c, int g, int g2, const Vtx *x, Vtx *y, int a, int b, int cc,
+static __device__ __noinline__ int map_step(Ctx &c, int g, int g2, const Vtx *x, Vtx *y, int a, int b, int cc,
                         MapInfo &mi) {
     if (same3(y[a].p, x[a].p)) {               // predecessor unchanged
         y[b] = x[b];
