@@ -459,7 +459,7 @@ static __device__ __forceinline__ float safe_rcp(float x) {
 }
 
 // The path-level routines below that trace rays or walk a whole path
-// (trace_next, segment_clear, ghost_crossings, path_throughput,
+// (trace_next, segment_clear, ghost_prims, ghost_geom, path_throughput,
 // mis_denominator, map_step) are kept out of line: the mapping kernel calls
 // each from several places, and inlined copies of the traversal loop in
 // every caller overflow the instruction cache when its lanes diverge.
@@ -767,15 +767,10 @@ static __device__ int traverse_all(const DevBVH &B, float3 o, float3 d, float tm
 
 constexpr int kMaxCross = 8;        // ghost crossings kept per edge
 
-// crossings of the open segment a-b of frame g with the ghost: the edited
-// object at its pose of the other frame (Sec. 3.3); positions and unit
-// normals in world space.  The normals are taken in double from the
-// triangle's world-space vertices, and each crossing point is re-solved in
-// double on the plane of the triangle the traversal found: the ghost
-// densities divide by |n . w|, and near the silhouette (where area sampling
-// of the ghost puts many samples) both that and the crossing's place on the
-// edge are ill-conditioned in single precision.
-static __device__ __noinline__ int ghost_crossings(Ctx &c, int g, float3 a, float3 b, double3 *cp, double3 *cn) {
+// ghost_prims: the triangles of the ghost (the edited objects at their pose
+// of the other frame, Sec. 3.3) that the open segment a-b of frame g
+// crosses, up to kMaxCross, with their distances.
+static __device__ __noinline__ int ghost_prims(Ctx &c, int g, float3 a, float3 b, float *ts, int *prims) {
     const DevScene &S = c.A.S;
     if (!c.A.E.motion) return 0;
     const int go = 3 - g;
@@ -783,8 +778,6 @@ static __device__ __noinline__ int ghost_crossings(Ctx &c, int g, float3 a, floa
     const float dist = len3(e);
     const float3 d = e * (1.0f / dist);
     const float tmin = S.eps, tmax = dist - S.eps;
-    float ts[kMaxCross];
-    int prims[kMaxCross];
     int n = 0;
     for (int k = 0; k < S.n_inst && n < kMaxCross; ++k) {
         const DevInst &I = S.inst[k];
@@ -794,19 +787,24 @@ static __device__ __noinline__ int ghost_crossings(Ctx &c, int g, float3 a, floa
         n += traverse_all(I.bvh, oo, dd, tmin, tmax, ts + n, prims + n, kMaxCross - n, c.stack,
                           c.cnt, &c.overflow, I.base);
     }
-    const double3 da = d3(a), dw = dunit(dsub(d3(b), da));
-    for (int i = 0; i < n; ++i) {
-        int k;
-        const float4 *tr = dyn_tri_of(S, prims[i], k);
-        const float *M = c.A.E.M(k, go);
-        const double3 v0 = daffine(M, d3(tr[0])), v1 = daffine(M, d3(tr[1])), v2 = daffine(M, d3(tr[2]));
-        const double3 nn = dcross(dsub(v1, v0), dsub(v2, v0));
-        const double den = ddot(nn, dw);
-        const double t = den != 0.0 ? ddot(nn, dsub(v0, da)) / den : (double)ts[i];
-        cp[i] = dadd(da, dscale(dw, t));
-        cn[i] = dunit(nn);
-    }
     return n;
+}
+
+// the crossing of the segment from da along unit dw with ghost triangle
+// prim (frame-go pose), re-solved in double on the triangle's plane
+// (tfall: the distance to use if the segment lies in the plane)
+static __device__ __forceinline__ void ghost_resolve(const Ctx &c, int go, double3 da, double3 dw,
+                                                     int prim, double tfall, double3 &cp,
+                                                     double3 &cn) {
+    int k;
+    const float4 *tr = dyn_tri_of(c.A.S, prim, k);
+    const float *M = c.A.E.M(k, go);
+    const double3 v0 = daffine(M, d3(tr[0])), v1 = daffine(M, d3(tr[1])), v2 = daffine(M, d3(tr[2]));
+    const double3 nn = dcross(dsub(v1, v0), dsub(v2, v0));
+    const double den = ddot(nn, dw);
+    const double t = den != 0.0 ? ddot(nn, dsub(v0, da)) / den : tfall;
+    cp = dadd(da, dscale(dw, t));
+    cn = dunit(nn);
 }
 
 // ---------------------------------------------------------------------------
@@ -1027,6 +1025,59 @@ static __device__ float step_pdf(const Ctx &c, int g, const Vtx *x, int cond, in
     return area_from_dir(bsdf_pdf(m, x[at].n, wc, wo), x[at].p, x[to]);
 }
 
+// The geometric factor of the term of ghost technique `kind` (4: last
+// edge, 5: first edge, 6: in between) for the crossing of edge j of x with
+// ghost triangle prim (the edited object at its frame 3 - g pose): the area
+// density of the vertex behind a ghost point sampled by area (Eq.
+// vertex1pdf) without p_D, or for (6) the two-ends geometric term with the
+// uniform direction density 1 / 4 pi.  Single precision, except where the
+// edge grazes the triangle (|cos| < 0.05): there the factor's 1 / |cos| and
+// the crossing's place on the edge amplify rounding, and the crossing is
+// re-solved and the factor taken in double.  0 when the edge lies in the
+// triangle's plane.
+static __device__ __noinline__ double ghost_geom(const Ctx &c, int g, const Vtx *x, int k, int j,
+                                                 int kind, int prim, float tfall) {
+    int kk;
+    const float4 *tr = dyn_tri_of(c.A.S, prim, kk);
+    const float *M = c.A.E.M(kk, 3 - g);
+    const float3 a = x[j].p, e = x[j + 1].p - a;
+    const float el2 = dot3(e, e);
+    const float3 w = e * (1.0f / sqrtf(el2));
+    const float3 v0 = affine(M, xyz(tr[0])), v1 = affine(M, xyz(tr[1])), v2 = affine(M, xyz(tr[2]));
+    const float3 nn = cross3(v1 - v0, v2 - v0);
+    const float nl = len3(nn);
+    const float den = dot3(nn, w);
+    if (fabsf(den) >= 0.05f * nl) {
+        if (kind == 6)
+            return (double)(fabsf(dot3(x[j].n, w)) * fabsf(dot3(x[j + 1].n, w))) /
+                   ((double)(fabsf(den) / nl) * 4.0 * kPiD * (double)el2);
+        const float3 cp = a + w * (dot3(nn, v0 - a) / den);
+        const float3 o = (kind == 4) ? x[k - 1].p : x[0].p;
+        const Vtx &x1 = (kind == 4) ? x[k - 2] : x[1];
+        const float3 o1 = x1.p - o, og = cp - o;
+        const float3 wo = o1 * (1.0f / len3(o1));
+        const float cg = fabsf(dot3(nn, wo)) / nl, c1 = fabsf(dot3(x1.n, wo));
+        if (!(cg > 0.f)) return 0.0;
+        return (double)dot3(og, og) * (double)c1 / ((double)cg * (double)dot3(o1, o1));
+    }
+    const double3 da = d3(a), dw = dunit(dsub(d3(x[j + 1].p), da));
+    double3 cp, cn;
+    ghost_resolve(c, 3 - g, da, dw, prim, (double)tfall, cp, cn);
+    if (kind == 6) {
+        const double cg = fabs(ddot(cn, dw));
+        if (!(cg > 0.0)) return 0.0;
+        const double3 ed = dsub(d3(x[j + 1].p), da);
+        return fabs(ddot(d3(x[j].n), dw)) * fabs(ddot(d3(x[j + 1].n), dw)) / (cg * 4.0 * kPiD * ddot(ed, ed));
+    }
+    const double3 o = d3((kind == 4) ? x[k - 1].p : x[0].p);
+    const Vtx &x1 = (kind == 4) ? x[k - 2] : x[1];
+    const double3 o1 = dsub(d3(x1.p), o), wo = dunit(o1);
+    const double cg = fabs(ddot(cn, wo)), c1 = fabs(ddot(d3(x1.n), wo));
+    if (!(cg > 0.0)) return 0.0;
+    const double3 og = dsub(cp, o);
+    return ddot(og, og) * c1 / (cg * ddot(o1, o1));
+}
+
 // the balance-heuristic denominator of a path: the sum over the enabled
 // techniques that can produce it of their area densities (Sec. 4.3), each a
 // product of single-precision factors kept as SF
@@ -1083,36 +1134,26 @@ static __device__ __noinline__ SF mis_denominator(Ctx &c, int g, const Vtx *x, i
         for (int j = 0; j <= k - 2; ++j) {
             const int kind = (j == 0) ? 5 : (j == k - 2) ? 4 : 6;
             if (!(tm & (1 << kind)) || ((known_clear >> j) & 1u)) continue;
-            double3 cp[kMaxCross], cn[kMaxCross];
-            const int nc = ghost_crossings(c, g, x[j].p, x[j + 1].p, cp, cn);
+            float ts[kMaxCross];
+            int prims[kMaxCross];
+            const int nc = ghost_prims(c, g, x[j].p, x[j + 1].p, ts, prims);
             if (searched) *searched |= 1u << j;
             if (crossed && nc > 0) *crossed |= 1u << j;
+            if (nc == 0) continue;
+            // the walk densities the technique shares for every crossing of
+            // this edge
+            SF base{pD * pLi, 0};
+            if (kind == 4) {
+                for (int m = 1; m <= k - 3; ++m) base = sf_mul(base, pL[m]);
+            } else if (kind == 5) {
+                for (int m = 2; m <= k - 2; ++m) base = sf_mul(base, pE[m]);
+            } else {
+                for (int m = 1; m <= j - 1; ++m) base = sf_mul(base, pL[m]);
+                for (int m = j + 2; m <= k - 2; ++m) base = sf_mul(base, pE[m]);
+            }
             for (int q = 0; q < nc; ++q) {
-                SF p{pD * pLi, 0};
-                if (kind == 4 || kind == 5) {
-                    const double3 o = d3((kind == 4) ? x[k - 1].p : x[0].p);
-                    const Vtx &x1 = (kind == 4) ? x[k - 2] : x[1];
-                    const double3 o1 = dsub(d3(x1.p), o), w = dunit(o1);
-                    const double cg = fabs(ddot(cn[q], w)), c1 = fabs(ddot(d3(x1.n), w));
-                    if (!(cg > 0.0)) continue;
-                    const double3 og = dsub(cp[q], o);
-                    p = sf_mul_d(p, ddot(og, og) * c1 / (cg * ddot(o1, o1)));
-                    if (kind == 4) {
-                        for (int m = 1; m <= k - 3; ++m) p = sf_mul(p, pL[m]);
-                    } else {
-                        for (int m = 2; m <= k - 2; ++m) p = sf_mul(p, pE[m]);
-                    }
-                } else {
-                    const double3 e = dsub(d3(x[j + 1].p), d3(x[j].p));
-                    const double3 w = dunit(e);
-                    const double cg = fabs(ddot(cn[q], w));
-                    if (!(cg > 0.0)) continue;
-                    p = sf_mul_d(p, fabs(ddot(d3(x[j].n), w)) * fabs(ddot(d3(x[j + 1].n), w)) /
-                                        (cg * 4.0 * kPi * ddot(e, e)));
-                    for (int m = 1; m <= j - 1; ++m) p = sf_mul(p, pL[m]);
-                    for (int m = j + 2; m <= k - 2; ++m) p = sf_mul(p, pE[m]);
-                }
-                sum = sf_add(sum, p);
+                const double gf = ghost_geom(c, g, x, k, j, kind, prims[q], ts[q]);
+                if (gf > 0.0) sum = sf_add(sum, sf_mul_d(base, gf));
             }
         }
     }
