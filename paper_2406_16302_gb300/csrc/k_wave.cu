@@ -986,7 +986,9 @@ cudaError_t run_wave(const LaunchArgs &a, cudaStream_t s) {
             RP_LAUNCH("k_enum", gE, 128, k_enum<T>, a);
             map_stage(a, s, gQ);
         } else {
-            RP_LAUNCH("k_eval", gE, 128, k_eval_fast<T>, a);
+            // per-technique names in the kernel timings
+            const char *ename = T == T_1 ? "k_eval_t1" : T == T_2 ? "k_eval_t2" : T == T_3 ? "k_eval_t3" : "k_eval_pt";
+            RP_LAUNCH(ename, gE, 128, k_eval_fast<T>, a);
         }
     }
     return cudaGetLastError();
