@@ -322,6 +322,16 @@ rp_status rp_guide_get_int(rp_guide *guide, int8_t *weights, int32_t *shift, int
 rp_status rp_guide_infer(rp_guide *guide, const int8_t *d_in, uint32_t n, float *d_out,
                          void *stream);
 
+/* The network's input features of n object-space points d_p[n][3] (double)
+ * with unit normals d_n[n][3] (float), in the guide's box: for each
+ * coordinate of u = clamp((p - center) * inv_half, -1, 1) and of the normal,
+ * sin and cos of 2^f pi x for f = 0..5, then u and the normal, each
+ * quantised to rint(128 e) in [-127, 127], then 127 and 0: d_out[n][80]
+ * (int8), the rows rp_guide_infer takes and technique (3) computes for x_D.
+ * Asynchronous.  Errors: RP_ERR_INVALID_ARG, RP_ERR_CUDA. */
+rp_status rp_guide_encode(rp_guide *guide, const double *d_p, const float *d_n, uint32_t n,
+                          int8_t *d_out, void *stream);
+
 /* Float network: the mean loss (1/n) sum_i -wt_i log q_vmf(w_i) of n rows
  * (d_x[n][80] features, rounded to BF16; d_omega[n][3] unit directions;
  * d_wt[n] weights; rows with wt <= 0 add nothing) and its gradient with

@@ -62,6 +62,9 @@ cudaError_t launch_guide_features(const GuideSamples &smp, const float *box, uin
                                   __nv_bfloat16 *X, float *omega, float *wt, float *wsum,
                                   cudaStream_t s);
 cudaError_t launch_f32_to_bf16(const float *src, __nv_bfloat16 *dst, size_t n, cudaStream_t s);
+// input features of n points (double) and normals (float): out[n][80]
+cudaError_t launch_guide_encode(const float *box, const double *p, const float *nrm, uint32_t n,
+                                int8_t *out, cudaStream_t s);
 cudaError_t launch_guide_adam(float *W, float *m, float *v, const float *grad,
                               __nv_bfloat16 *Wbf, int n, float lr, float b1, float b2, float eps,
                               float c1, float c2, cudaStream_t s);

@@ -12,7 +12,16 @@ namespace rp {
 // input features of an object-space point and (float) unit normal: for each
 // coordinate c of u = clamp((p - center) inv_half, -1, 1), then of n,
 // sin(2^f pi c), cos(2^f pi c) for f = 0..5; then u and n; quantised to
-// rint(128 e) in [-127, 127]; then the constant 127 and a zero
+// rint(128 e) in [-127, 127]; then the constant 127 and a zero.
+// The argument a = 2^f c is reduced to r = a - 2 rint(a / 2) in [-1, 1] in
+// single precision: c = ch + cl with ch = (float) c, the high part's
+// reduction 2^f ch - 2 rintf(2^f ch / 2) is exact (|2^f ch| <= 32, and an
+// even integer subtracted from it leaves a representable value), and the
+// low part 2^f cl adds a rounding of at most one ulp of r.  sin(pi r) and
+// cos(pi r) are then taken in single precision: their error in 128 e stays
+// below 1e-4, so the quantised value is the one the double-precision sine
+// gives unless 128 e lies within 1e-3 of a rounding boundary, where it is
+// recomputed in double from the exact argument.
 static __device__ void guide_encode_d(const float *box, double3 p, float3 n, int8_t *m) {
     double u[3] = {((double)p.x - box[0]) * box[3], ((double)p.y - box[1]) * box[4],
                    ((double)p.z - box[2]) * box[5]};
@@ -23,19 +32,29 @@ static __device__ void guide_encode_d(const float *box, double3 p, float3 n, int
         const double r = rint(128.0 * e);
         return (int8_t)(int)fmin(127.0, fmax(-127.0, r));
     };
-    // one sincospi per coordinate, then the double-angle formulas
-    // sin 2a = 2 sin a cos a, cos 2a = cos^2 a - sin^2 a: five doublings keep
-    // the error within a few 1e-15, far below the quantisation step 1/128
+    auto near_half = [](float e) {
+        const float v = 128.0f * e;
+        return fabsf(v - floorf(v) - 0.5f) < 1e-3f;
+    };
     for (int v = 0; v < 2; ++v)
         for (int c = 0; c < 3; ++c) {
-            double s, co;
-            sincospi(v == 0 ? u[c] : nn[c], &s, &co);
+            const double x = v == 0 ? u[c] : nn[c];
+            const float xh = (float)x, xl = (float)(x - (double)xh);
             for (int f = 0; f < 6; ++f) {
-                m[i++] = q(s);
-                m[i++] = q(co);
-                const double s2 = 2.0 * s * co, c2 = co * co - s * s;
-                s = s2;
-                co = c2;
+                const float ah = ldexpf(xh, f);
+                const float r = (ah - 2.0f * rintf(0.5f * ah)) + ldexpf(xl, f);
+                float sf, cf;
+                sincospif(r, &sf, &cf);
+                if (near_half(sf) || near_half(cf)) {
+                    const double a = ldexp(x, f);
+                    double sd, cd;
+                    sincospi(a - 2.0 * rint(0.5 * a), &sd, &cd);
+                    m[i++] = q(sd);
+                    m[i++] = q(cd);
+                } else {
+                    m[i++] = (int8_t)(int)fminf(127.0f, fmaxf(-127.0f, rintf(128.0f * sf)));
+                    m[i++] = (int8_t)(int)fminf(127.0f, fmaxf(-127.0f, rintf(128.0f * cf)));
+                }
             }
         }
     for (int c = 0; c < 3; ++c) m[i++] = q(u[c]);

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
                     // network's input and the training samples (edits of one
                     // object only)
                     const float4 ur = draw(lseed(A), root, T_3, g, SD_ROOT, 0);
-                    const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
+                    const int q = xD.prim - A.S.n_static;
                     double b1, b2;
                     tri_sample(ur.y, ur.z, b1, b2);
                     const float4 *tq = A.S.inst[0].tri + 3 * q;
@@ -223,6 +223,20 @@ __global__ void __launch_bounds__(256) k_gen(const __grid_constant__ LaunchArgs 
     }
 }
 
+namespace {
+// one row of input features, built locally and written as five 16-byte
+// vectors (a row is 80 bytes, rows are 16-byte aligned)
+__device__ __forceinline__ void store_features(int8_t *dst, const float *box, double3 p, float3 n) {
+    alignas(16) int8_t m[kGIn];
+    guide_encode_d(box, p, n, m);
+    const int4 *src = reinterpret_cast<const int4 *>(m);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+#pragma unroll
+    for (int k = 0; k < kGIn / 16; ++k) d[k] = src[k];
+}
+
+}  // namespace
+
 // technique (3) with the learned proposal: the network's integer input
 // features of x_D (object space, recomputed from the root's numbers)
 __global__ void __launch_bounds__(128) k_encode3(const __grid_constant__ LaunchArgs A) {
@@ -232,15 +246,48 @@ __global__ void __launch_bounds__(128) k_encode3(const __grid_constant__ LaunchA
         if (!(A.W.flags[r] & RF_GUIDE)) continue;
         const uint32_t root = A.root_begin + r;
         const float4 ur = draw(lseed(A), root, T_3, g, SD_ROOT, 0);
-        const int q = cdf_pick(A.S.dyn_cdf, A.S.n_dyn, ur.x);
+        // x_D's triangle, as k_gen picked it (slot 0); its barycentrics in
+        // double again from the root's numbers
+        const int q = A.W.prim[r] - A.S.n_static;
         double b1, b2;
         tri_sample(ur.y, ur.z, b1, b2);
         const float4 *tq = A.S.inst[0].tri + 3 * q;
         const float4 ta = tq[0], tb = tq[1], tcv = tq[2];
         const double3 v0 = d3(ta);
         const double3 po = dadd(dadd(v0, dscale(dsub(d3(tb), v0), b1)), dscale(dsub(d3(tcv), v0), b2));
-        guide_encode_d(A.G.net.box, po, f3(ta.w, tb.w, tcv.w), A.G.gin + (size_t)r * kGIn);
+        store_features(A.G.gin + (size_t)r * kGIn, A.G.net.box, po, f3(ta.w, tb.w, tcv.w));
     }
+}
+
+namespace {
+struct EncodeArgs {
+    float box[6];
+    const double *p;
+    const float *nrm;
+    uint32_t n;
+    int8_t *out;
+};
+}  // namespace
+
+// the learned proposal's input features of given points (rp_guide_encode)
+__global__ void __launch_bounds__(128) k_guide_encode(const __grid_constant__ EncodeArgs E) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < E.n; i += gridDim.x * blockDim.x)
+        store_features(E.out + (size_t)i * kGIn, E.box, d3(E.p[3 * i], E.p[3 * i + 1], E.p[3 * i + 2]),
+                       f3(E.nrm[3 * i], E.nrm[3 * i + 1], E.nrm[3 * i + 2]));
+}
+
+cudaError_t launch_guide_encode(const float *box, const double *p, const float *nrm, uint32_t n,
+                                int8_t *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    EncodeArgs E;
+    for (int k = 0; k < 6; ++k) E.box[k] = box[k];
+    E.p = p;
+    E.nrm = nrm;
+    E.n = n;
+    E.out = out;
+    const uint32_t g = (n + 127) / 128;
+    k_guide_encode<<<g < 4096u ? g : 4096u, 128, 0, s>>>(E);
+    return cudaGetLastError();
 }
 
 // technique (3) with the learned proposal: draw the first light-side

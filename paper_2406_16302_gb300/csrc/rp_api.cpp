@@ -1179,6 +1179,13 @@ extern "C" rp_status rp_guide_infer(rp_guide *g, const int8_t *d_in, uint32_t n,
     return RP_OK;
 }
 
+extern "C" rp_status rp_guide_encode(rp_guide *g, const double *d_p, const float *d_n, uint32_t n,
+                                    int8_t *d_out, void *stream) {
+    if (!g || (n && (!d_p || !d_n || !d_out))) return fail(RP_ERR_INVALID_ARG, "null argument");
+    RP_CUDA(launch_guide_encode(g->box, d_p, d_n, n, d_out, (cudaStream_t)stream), "guide encoding");
+    return RP_OK;
+}
+
 extern "C" rp_status rp_guide_loss_grad(rp_guide *g, const float *d_x, const float *d_omega,
                                         const float *d_wt, uint32_t n, float *d_grad, float *d_loss,
                                         void *stream) {

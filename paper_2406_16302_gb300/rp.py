@@ -81,7 +81,7 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_multi", "r
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
            "rp_enable_stats", "rp_get_stats", "rp_enable_timing", "rp_get_kernel_times",
            "rp_guide_create", "rp_guide_destroy", "rp_guide_set_weights", "rp_guide_get_weights",
-           "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_loss_grad",
+           "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_encode", "rp_guide_loss_grad",
            "rp_guide_train_step", "rp_guide_status", "rp_scene_set_guide",
            "rp_batch_create", "rp_batch_destroy", "rp_batch_launch", "rp_batch_set_seeds",
            "rp_batch_info", "rp_batch_autotune", "rp_scene_set_mapping",
@@ -107,6 +107,7 @@ def lib():
         "rp_scene_destroy": (None, [P]),
         "rp_edit": (I, [P, P, P]),
         "rp_edit_multi": (I, [P, P, C.c_uint32, P]),
+        "rp_guide_encode": (I, [P, P, P, C.c_uint32, P, P]),
         "rp_edit_destroy": (None, [P]),
         "rp_render_residual": (I, [P, P, U32, U64, U32, P, P]),
         "rp_render_residual_f32": (I, [P, P, U32, U64, U32, P, P]),
@@ -391,6 +392,13 @@ def rp_guide_get_int(guide: Guide):
 def rp_guide_infer(guide: Guide, m_in, out, stream=None):
     """m_in: int8 tensor [n][80] on the device; out: float32 tensor [n][48]."""
     _check(lib().rp_guide_infer(guide.h, _ptr(m_in), m_in.shape[0], _ptr(out), _stream(stream)))
+
+
+def rp_guide_encode(guide: Guide, points, normals, out, stream=None):
+    """Input features of object-space points (float64 [n][3]) and unit
+    normals (float32 [n][3]) into out (int8 [n][80]); device tensors."""
+    _check(lib().rp_guide_encode(guide.h, _ptr(points), _ptr(normals), int(points.shape[0]),
+                                 _ptr(out), _stream(stream)))
 
 
 def rp_guide_loss_grad(guide: Guide, x, omega, wt, grad, loss, stream=None):

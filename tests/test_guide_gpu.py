@@ -68,6 +68,37 @@ def test_integer_inference_of_encoded_points(rp):
     assert np.array_equal(d_out.cpu().numpy().astype(np.float64), O.guide_forward(W, sh, oe, m))
 
 
+def test_encoding_matches_oracle(rp):
+    """The GPU feature encoding (single-precision sines of an exactly reduced
+    argument, double precision near rounding boundaries) against the
+    oracle's double-precision encoding, feature by feature: random points,
+    and points placed so that one feature lies within 1e-9 of a rounding
+    boundary of rint(128 e)."""
+    import torch
+    box = np.array([0.1, -0.2, 0.3, 2.5, 1.7, 3.1], np.float32)   # center, inverse half extent
+    g = rp.Guide(box, batch=256)
+    rng = np.random.default_rng(17)
+    n_rand, n_edge = 4000, 3000
+    u = rng.uniform(-1.05, 1.05, size=(n_rand + n_edge, 3))
+    # boundary cases: sin(pi 2^f u_x) = (k + 1/2) / 128 +- 1e-9
+    f = rng.integers(0, 6, size=n_edge)
+    k = rng.integers(-127, 127, size=n_edge)
+    e = (k + 0.5) / 128.0 + rng.choice([-1e-9, 1e-9], size=n_edge)
+    a = np.arcsin(np.clip(e, -1, 1)) / np.pi + rng.integers(-3, 4, size=n_edge) * 2.0
+    u[n_rand:, 0] = np.clip(a / 2.0 ** f, -1.0, 1.0)
+    center = box[:3].astype(np.float64)
+    inv_half = box[3:].astype(np.float64)
+    pts = center + u / inv_half
+    nrm = rng.normal(size=(len(pts), 3))
+    nrm = (nrm / np.linalg.norm(nrm, axis=1, keepdims=True)).astype(np.float32)
+    out = torch.zeros((len(pts), 80), dtype=torch.int8, device="cuda")
+    rp.rp_guide_encode(g, torch.from_numpy(pts).cuda(), torch.from_numpy(nrm).cuda(), out)
+    got = out.cpu().numpy().astype(np.int32)
+    want = np.array([O.guide_encode(box, p_, n_.astype(np.float64)) for p_, n_ in zip(pts, nrm)])
+    bad = np.argwhere(got != want)
+    assert len(bad) == 0, (len(bad), bad[:5], got[bad[0][0]][bad[0][1]], want[bad[0][0]][bad[0][1]])
+
+
 @pytest.mark.parametrize("rows", [200, 1000])
 def test_training_gradient_matches_oracle(rp, rows):
     """Loss and weight gradient of the float network: BF16 tensor-core
