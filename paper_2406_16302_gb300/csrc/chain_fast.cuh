@@ -251,6 +251,294 @@ __device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *z, in
     }
 }
 
+// Running states of fast_eye and fast_light for both frames, advanced one
+// walk vertex at a time (the streaming evaluators below read the walk's
+// vertices where they are needed instead of copying whole walks into
+// thread-local arrays).  Each frame's products, their updates and the
+// power-of-two rescaling (exponent chosen in frame 0, applied to both)
+// follow fast_eye and fast_light step by step.
+struct EyeRun {
+    float3 rho[2];
+    float Pf[2], Pz[2], Sz[2];
+    __device__ void init() {
+        for (int f = 0; f < 2; ++f) {
+            rho[f] = f3(1.f, 1.f, 1.f);
+            Pf[f] = Pz[f] = 1.f;
+            Sz[f] = 0.f;
+        }
+    }
+    // E(m), A(m), Pz(m) of the camera connection at z_m (zp = z_m-1)
+    __device__ void cam_values(const Ctx &cx, const int *frames, int mask, float pD,
+                               const fast_detail::CamTerm &ct, const Vtx &camv, const Vtx &zm,
+                               const Vtx &zp, float G, bool dyn, float3 *E, float *A,
+                               float *Pzt) const {
+        using namespace chain_detail;
+        for (int f = 0; f < 2; ++f) {
+            const Mat mm = get_mat(cx, frames[f], zm.mat);
+            const float pEC = pdf3(mm, camv, zm, zp);
+            E[f] = mul3(rho[f], rho3(mm, camv, zm, zp)) * (ct.we * G);
+            A[f] = ((mask & 8) ? ct.pcam * pEC * Pf[f] : 0.f) +
+                   ((mask & 2) && dyn ? pD * pEC * Pf[f] : 0.f) + ((mask & 4) ? pD * Sz[f] : 0.f);
+            Pzt[f] = Pz[f];
+        }
+    }
+    // from z_m to z_m+1 = zn
+    __device__ void advance(const Ctx &cx, const int *frames, const Vtx &zm, const Vtx &zp,
+                            const Vtx &zn, float G, bool dyn) {
+        using namespace chain_detail;
+        int sh = 0;
+        for (int f = 0; f < 2; ++f) {
+            const Mat mm = get_mat(cx, frames[f], zm.mat);
+            const float pLI = pdf3(mm, zp, zm, zn);
+            if (dyn) Sz[f] += area_from_dir(cosine_pdf(zm.n, unit3(zp.p - zm.p)), zm.p, zp) * Pf[f];
+            Sz[f] *= pLI;
+            rho[f] = mul3(rho[f], rho3(mm, zn, zm, zp)) * G;
+            Pf[f] *= pdf3(mm, zn, zm, zp);
+            Pz[f] *= pLI;
+            if (f == 0)
+                sh = fast_detail::rescale_exp(fmaxf(fmaxf(fmaxf(rho[0].x, rho[0].y), fmaxf(rho[0].z, Pf[0])),
+                                                    fmaxf(Pz[0], Sz[0])));
+            if (sh) {
+                const float sc = ldexpf(1.f, sh);
+                rho[f] = rho[f] * sc; Pf[f] *= sc; Pz[f] *= sc; Sz[f] *= sc;
+            }
+        }
+    }
+};
+
+struct LightRun {
+    float3 rho[2];
+    float Py[2], PLy[2], Sy[2];
+    __device__ void init() {
+        for (int f = 0; f < 2; ++f) {
+            rho[f] = f3(1.f, 1.f, 1.f);
+            Py[f] = PLy[f] = 1.f;
+            Sy[f] = 0.f;
+        }
+    }
+    // Ly(m), Py(m), B(m) of the next-event connection of y_m to Ls (yp = y_m-1)
+    __device__ void nee_values(const Ctx &cx, const int *frames, int mask, float pD, float pcosD,
+                               const Vtx &ym, const Vtx &yp, const Vtx &Ls, bool dyn, float3 *L,
+                               float *Pyt, float *B) const {
+        using namespace chain_detail;
+        for (int f = 0; f < 2; ++f) {
+            const Mat mm = get_mat(cx, frames[f], ym.mat);
+            L[f] = mul3(mul3(rho[f], rho3(mm, yp, ym, Ls)) * G2(ym, Ls), get_mat(cx, frames[f], Ls.mat).em);
+            Pyt[f] = Py[f];
+            const float pLL = pdf3(mm, Ls, ym, yp);
+            B[f] = ((mask & 4) ? pD * (pcosD * Py[f] + Sy[f]) : 0.f) +
+                   ((mask & 1) && dyn ? pD * PLy[f] * pLL : 0.f);
+        }
+    }
+    // from y_m to y_m+1 = yn
+    __device__ void advance(const Ctx &cx, const int *frames, const Vtx &ym, const Vtx &yp,
+                            const Vtx &yn, bool dyn) {
+        using namespace chain_detail;
+        int sh = 0;
+        for (int f = 0; f < 2; ++f) {
+            const Mat mm = get_mat(cx, frames[f], ym.mat);
+            const float pLI = pdf3(mm, yn, ym, yp);
+            const float pEI = pdf3(mm, yp, ym, yn);
+            PLy[f] *= pLI;
+            Sy[f] *= pEI;
+            if (dyn) Sy[f] += area_from_dir(cosine_pdf(ym.n, unit3(yn.p - ym.p)), ym.p, yn) * PLy[f];
+            rho[f] = mul3(rho[f], rho3(mm, yp, ym, yn)) * G2(ym, yn);
+            Py[f] *= pEI;
+            if (f == 0)
+                sh = fast_detail::rescale_exp(fmaxf(fmaxf(fmaxf(rho[0].x, rho[0].y), fmaxf(rho[0].z, Py[0])),
+                                                    fmaxf(PLy[0], Sy[0])));
+            if (sh) {
+                const float sc = ldexpf(1.f, sh);
+                rho[f] = rho[f] * sc; Py[f] *= sc; PLy[f] *= sc; Sy[f] *= sc;
+            }
+        }
+    }
+};
+
+// technique (3), the values of fast_t3: the eye-side state advances along
+// t and, for each t with a camera connection, the light-side state is
+// rebuilt along s (the light walk's factors are recomputed for every t
+// rather than stored per vertex).  Vertices come from ld.vtx(slot),
+// ld.eye(m), ld.light(m), ld.nee(m).
+template <class Ld>
+__device__ void fast_t3_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
+                               uint32_t cam, int ny, uint32_t nee) {
+    using namespace chain_detail;
+    using namespace fast_detail;
+    const LaunchArgs &A = cx.A;
+    const DevScene &Sc = A.S;
+    const int g = A.frame, D = Sc.max_depth, mask = A.tech_mask;
+    const int frames[2] = {g, 3 - g};
+    const float pLi = 1.0f / Sc.emit_area, pD = 1.0f / Sc.dyn_area;
+    const Vtx xD = ld.vtx(0);
+    const Vtx y1 = ld.light(1);
+    Vtx zm = ld.eye(1), zp = xD;
+    const float pcosD = area_from_dir(cosine_pdf(xD.n, unit3(y1.p - xD.p)), xD.p, y1);
+    const float Gd = G2(xD, y1);
+    float3 rD[2];
+    float pE[2], pL[2];
+    for (int f = 0; f < 2; ++f) {
+        const Mat m = get_mat(cx, frames[f], xD.mat);
+        rD[f] = rho3(m, zm, xD, y1) * Gd;
+        pE[f] = pdf3(m, zm, xD, y1);
+        pL[f] = pdf3(m, y1, xD, zm);
+    }
+    const Vtx camv = camera_vertex(cx);
+    EyeRun er;
+    er.init();
+    for (int t = 1; t <= nz; ++t) {
+        const float G = G2(zm, zp);
+        const bool dynz = is_dyn(cx, zm);
+        if (cam & (1u << t)) {
+            const CamTerm ct = cam_term(Sc, camv, zm);
+            float3 E[2];
+            float At[2], Pzt[2];
+            er.cam_values(cx, frames, mask, pD, ct, camv, zm, zp, G, dynz, E, At, Pzt);
+            LightRun lr;
+            lr.init();
+            Vtx ym = y1, yp = xD;
+            for (int s = 1; s <= ny && t + s <= D - 2; ++s) {
+                const bool dyny = is_dyn(cx, ym);
+                if (nee & (1u << s)) {
+                    float3 Ly[2];
+                    float Pyt[2], B[2];
+                    lr.nee_values(cx, frames, mask, pD, pcosD, ym, yp, ld.nee(s), dyny, Ly, Pyt, B);
+                    float3 fv[2];
+                    float P[2];
+                    for (int f = 0; f < 2; ++f) {
+                        fv[f] = mul3(mul3(E[f], rD[f]), Ly[f]);
+                        P[f] = pLi * (pE[f] * Pyt[f] * At[f] + pL[f] * Pzt[f] * B[f]);
+                    }
+                    emit_nomotion(cx, pc, root, T_3, t, s, ct.pix, fv[0], P[0], fv[1], P[1]);
+                }
+                if (s < ny && t + s + 1 <= D - 2) {
+                    const Vtx yn = ld.light(s + 1);
+                    lr.advance(cx, frames, ym, yp, yn, dyny);
+                    yp = ym;
+                    ym = yn;
+                }
+            }
+        }
+        if (t < nz) {
+            const Vtx zn = ld.eye(t + 1);
+            er.advance(cx, frames, zm, zp, zn, G, dynz);
+            zp = zm;
+            zm = zn;
+        }
+    }
+}
+
+// technique (1), the values of fast_t1, streaming the eye walk
+template <class Ld>
+__device__ void fast_t1_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
+                               uint32_t cam) {
+    using namespace chain_detail;
+    using namespace fast_detail;
+    const LaunchArgs &A = cx.A;
+    const DevScene &Sc = A.S;
+    const int g = A.frame, mask = A.tech_mask;
+    const int frames[2] = {g, 3 - g};
+    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
+    const Vtx xD = ld.vtx(0), xL = ld.vtx(1);
+    const float3 Le = get_mat(cx, g, xL.mat).em * G2(xD, xL);
+    const Vtx camv = camera_vertex(cx);
+    if (cam & 1u) {                              // t = 0: (camera, x_D, x_L)
+        const CamTerm ct = cam_term(Sc, camv, xD);
+        if (ct.we > 0.f) {
+            const float P = pLi * (((mask & 8) ? ct.pcam : 0.f) + ((mask & 1) ? pD : 0.f));
+            const float3 base = Le * ct.we;
+            emit_nomotion(cx, pc, root, T_1, 0, 0, ct.pix,
+                          mul3(base, rho3(get_mat(cx, frames[0], xD.mat), camv, xD, xL)), P,
+                          mul3(base, rho3(get_mat(cx, frames[1], xD.mat), camv, xD, xL)), P);
+        }
+    }
+    if (nz == 0) return;
+    Vtx zm = ld.eye(1), zp = xD;
+    float3 rD[2];
+    float pLL[2];
+    for (int f = 0; f < 2; ++f) {
+        const Mat m = get_mat(cx, frames[f], xD.mat);
+        rD[f] = mul3(rho3(m, zm, xD, xL), Le);
+        pLL[f] = pdf3(m, xL, xD, zm);
+    }
+    EyeRun er;
+    er.init();
+    for (int t = 1; t <= nz; ++t) {
+        const float G = G2(zm, zp);
+        const bool dynz = is_dyn(cx, zm);
+        if (cam & (1u << t)) {
+            const CamTerm ct = cam_term(Sc, camv, zm);
+            float3 E[2];
+            float At[2], Pzt[2];
+            er.cam_values(cx, frames, mask, pD, ct, camv, zm, zp, G, dynz, E, At, Pzt);
+            float3 fv[2];
+            float P[2];
+            for (int f = 0; f < 2; ++f) {
+                fv[f] = mul3(E[f], rD[f]);
+                P[f] = pLi * (At[f] + ((mask & 1) ? pD * Pzt[f] * pLL[f] : 0.f));
+            }
+            emit_nomotion(cx, pc, root, T_1, t, 0, ct.pix, fv[0], P[0], fv[1], P[1]);
+        }
+        if (t < nz) {
+            const Vtx zn = ld.eye(t + 1);
+            er.advance(cx, frames, zm, zp, zn, G, dynz);
+            zp = zm;
+            zm = zn;
+        }
+    }
+}
+
+// technique (2), the values of fast_t2, streaming the light walk
+template <class Ld>
+__device__ void fast_t2_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int ny,
+                               uint32_t nee) {
+    using namespace chain_detail;
+    using namespace fast_detail;
+    const LaunchArgs &A = cx.A;
+    const DevScene &Sc = A.S;
+    const int g = A.frame, mask = A.tech_mask;
+    const int frames[2] = {g, 3 - g};
+    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
+    const Vtx xD = ld.vtx(0);
+    const Vtx camv = camera_vertex(cx);
+    const CamTerm ct = cam_term(Sc, camv, xD);
+    if (ct.we <= 0.f || ny == 0) return;
+    Vtx ym = ld.light(1), yp = xD;
+    const float Gd = G2(xD, ym);
+    const float a = ((mask & 8) ? ct.pcam : 0.f) + ((mask & 2) ? pD : 0.f);
+    float3 rD[2];
+    float pEC[2];
+    for (int f = 0; f < 2; ++f) {
+        const Mat m = get_mat(cx, frames[f], xD.mat);
+        rD[f] = rho3(m, camv, xD, ym) * (ct.we * Gd);
+        pEC[f] = pdf3(m, camv, xD, ym);
+    }
+    LightRun lr;
+    lr.init();
+    for (int s = 1; s <= ny; ++s) {
+        const bool dyny = is_dyn(cx, ym);
+        if (nee & (1u << s)) {
+            float3 Ly[2];
+            float Pyt[2], B[2];
+            // x_D is technique (2) here: no technique-(3) term at x_D
+            lr.nee_values(cx, frames, mask, pD, 0.f, ym, yp, ld.nee(s), dyny, Ly, Pyt, B);
+            float3 fv[2];
+            float P[2];
+            for (int f = 0; f < 2; ++f) {
+                fv[f] = mul3(rD[f], Ly[f]);
+                P[f] = pLi * (a * pEC[f] * Pyt[f] + B[f]);
+            }
+            emit_nomotion(cx, pc, root, T_2, 0, s, ct.pix, fv[0], P[0], fv[1], P[1]);
+        }
+        if (s < ny) {
+            const Vtx yn = ld.light(s + 1);
+            lr.advance(cx, frames, ym, yp, yn, dyny);
+            yp = ym;
+            ym = yn;
+        }
+    }
+}
+
 // technique (1): paths (camera, z_t .. z_1, x_D, x_L), t = 0 .. nz
 __device__ void fast_t1(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *z, int nz, uint32_t cam,
                         const Vtx &xL) {

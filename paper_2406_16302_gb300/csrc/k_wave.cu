@@ -62,6 +62,18 @@ __device__ __forceinline__ Vtx load_vtx(const Ctx &c, const WaveBuf &W, int slot
     return v;
 }
 
+// a root's walk vertices read from its slots where they are needed
+struct SlotLoader {
+    const Ctx &c;
+    const WaveBuf &W;
+    uint32_t r;
+    int D;
+    __device__ Vtx vtx(int slot) const { return load_vtx(c, W, slot, r); }
+    __device__ Vtx eye(int m) const { return load_vtx(c, W, slot_eye(D, m), r); }
+    __device__ Vtx light(int m) const { return load_vtx(c, W, slot_light(D, m), r); }
+    __device__ Vtx nee(int m) const { return load_vtx(c, W, slot_nee(D, m), r); }
+};
+
 __device__ __forceinline__ void push_closest(const LaunchArgs &A, int buf, int it, float3 o,
                                              float3 d, int ex, uint32_t tag) {
     const WaveBuf &W = A.W;
@@ -689,6 +701,16 @@ __global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ Launc
         const int nz = (T == T_2) ? 0 : W.len_eye[r];
         const int ny = (T == T_1) ? 0 : W.len_light[r];
         if (T == T_3 && (nz == 0 || ny == 0)) continue;
+        if constexpr (T == T_3) {
+            fast_t3_stream(c, pc, root, SlotLoader{c, W, r, D}, nz, cam, ny, nee);
+            continue;
+        } else if constexpr (T == T_1) {
+            fast_t1_stream(c, pc, root, SlotLoader{c, W, r, D}, nz, cam);
+            continue;
+        } else if constexpr (T == T_2) {
+            fast_t2_stream(c, pc, root, SlotLoader{c, W, r, D}, ny, nee);
+            continue;
+        }
         zv[0] = load_vtx(c, W, 0, r);
         for (int m = 1; m <= nz; ++m) zv[m] = load_vtx(c, W, slot_eye(D, m), r);
         yv[0] = zv[0];
