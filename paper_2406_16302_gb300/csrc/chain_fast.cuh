@@ -63,19 +63,6 @@ __device__ __forceinline__ CamTerm cam_term(const DevScene &S, const Vtx &cam, c
     return c;
 }
 
-// eye side: for t = 1..nz with a camera connection, E(t) and A(t), Pz(t)
-struct Eye {
-    float3 E[2][kSide];
-    float A[2][kSide], Pz[2][kSide];
-    int pix[kSide];
-};
-
-// light side: for s = 1..ny with a next-event vertex, Ly(s), Py(s), B(s)
-struct Light {
-    float3 L[2][kSide];
-    float Py[2][kSide], B[2][kSide];
-};
-
 // Power-of-two rescaling of running products.  Near-coincident walk
 // vertices make geometric terms and area densities of 1e8 and more per edge,
 // so the products overflow single precision over a long walk.  Every value
@@ -121,142 +108,11 @@ __device__ __forceinline__ void emit_nomotion(Ctx &cx, PathCounts &pc, uint32_t 
     }
 }
 
-// eye side from x_D = z[0] (techniques (1) and (3))
-__device__ void fast_eye(const Ctx &cx, int nf, const int *frames, const Vtx *z, int nz,
-                         uint32_t cam, int mask, fast_detail::Eye &S) {
-    using namespace chain_detail;
-    using namespace fast_detail;
-    const DevScene &Sc = cx.A.S;
-    const Vtx camv = camera_vertex(cx);
-    const float pD = 1.0f / Sc.dyn_area;
-    int sh[kSide + 1];                  // rescaling exponents, chosen in the first frame
-    for (int f = 0; f < nf; ++f) {
-        float3 prho = f3(1.f, 1.f, 1.f);
-        float Pf = 1.f, Pz = 1.f, Sz = 0.f;
-        for (int m = 1; m <= nz; ++m) {
-            const Vtx &zm = z[m], &zp = z[m - 1];
-            const Mat mm = get_mat(cx, frames[f], zm.mat);
-            const float G = G2(zm, zp);
-            const bool dyn = is_dyn(cx, zm);
-            if (cam & (1u << m)) {
-                const CamTerm ct = cam_term(Sc, camv, zm);
-                if (f == 0) S.pix[m] = ct.pix;
-                const float pEC = pdf3(mm, camv, zm, zp);
-                S.E[f][m] = mul3(prho, rho3(mm, camv, zm, zp)) * (ct.we * G);
-                S.A[f][m] = ((mask & 8) ? ct.pcam * pEC * Pf : 0.f) +
-                            ((mask & 2) && dyn ? pD * pEC * Pf : 0.f) + ((mask & 4) ? pD * Sz : 0.f);
-                S.Pz[f][m] = Pz;
-            }
-            if (m < nz) {
-                const Vtx &zn = z[m + 1];
-                const float pLI = pdf3(mm, zp, zm, zn);
-                if (dyn)
-                    Sz += area_from_dir(cosine_pdf(zm.n, unit3(zp.p - zm.p)), zm.p, zp) * Pf;
-                Sz *= pLI;
-                prho = mul3(prho, rho3(mm, zn, zm, zp)) * G;
-                Pf *= pdf3(mm, zn, zm, zp);
-                Pz *= pLI;
-                if (f == 0)
-                    sh[m] = rescale_exp(fmaxf(fmaxf(fmaxf(prho.x, prho.y), fmaxf(prho.z, Pf)),
-                                              fmaxf(Pz, Sz)));
-                if (sh[m]) {
-                    const float sc = ldexpf(1.f, sh[m]);
-                    prho = prho * sc; Pf *= sc; Pz *= sc; Sz *= sc;
-                }
-            }
-        }
-    }
-}
-
-// light side from x_D = y[0] (techniques (2) and (3)); `with_dcos` adds the
-// technique-(3) term of x_D itself (pD pcos(x_D) Py)
-__device__ void fast_light(const Ctx &cx, int nf, const int *frames, const Vtx *y, const Vtx *L,
-                           int ny, uint32_t nee, int mask, float pcosD, fast_detail::Light &S) {
-    using namespace chain_detail;
-    using namespace fast_detail;
-    const DevScene &Sc = cx.A.S;
-    const float pD = 1.0f / Sc.dyn_area;
-    int sh[kSide + 1];                  // rescaling exponents, chosen in the first frame
-    for (int f = 0; f < nf; ++f) {
-        float3 prho = f3(1.f, 1.f, 1.f);
-        float Py = 1.f, PLy = 1.f, Sy = 0.f;
-        for (int m = 1; m <= ny; ++m) {
-            const Vtx &ym = y[m], &yp = y[m - 1];
-            const Mat mm = get_mat(cx, frames[f], ym.mat);
-            const bool dyn = is_dyn(cx, ym);
-            if (nee & (1u << m)) {
-                S.L[f][m] = mul3(mul3(prho, rho3(mm, yp, ym, L[m])) * G2(ym, L[m]),
-                                 get_mat(cx, frames[f], L[m].mat).em);
-                S.Py[f][m] = Py;
-                const float pLL = pdf3(mm, L[m], ym, yp);
-                S.B[f][m] = ((mask & 4) ? pD * (pcosD * Py + Sy) : 0.f) +
-                            ((mask & 1) && dyn ? pD * PLy * pLL : 0.f);
-            }
-            if (m < ny) {
-                const Vtx &yn = y[m + 1];
-                const float pLI = pdf3(mm, yn, ym, yp);
-                const float pEI = pdf3(mm, yp, ym, yn);
-                PLy *= pLI;
-                Sy *= pEI;
-                if (dyn) Sy += area_from_dir(cosine_pdf(ym.n, unit3(yn.p - ym.p)), ym.p, yn) * PLy;
-                prho = mul3(prho, rho3(mm, yp, ym, yn)) * G2(ym, yn);
-                Py *= pEI;
-                if (f == 0)
-                    sh[m] = rescale_exp(fmaxf(fmaxf(fmaxf(prho.x, prho.y), fmaxf(prho.z, Py)),
-                                              fmaxf(PLy, Sy)));
-                if (sh[m]) {
-                    const float sc = ldexpf(1.f, sh[m]);
-                    prho = prho * sc; Py *= sc; PLy *= sc; Sy *= sc;
-                }
-            }
-        }
-    }
-}
-
-// technique (3): all (t, s) paths of one root
-__device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *z, int nz, uint32_t cam,
-                        const Vtx *y, const Vtx *L, int ny, uint32_t nee) {
-    using namespace chain_detail;
-    const LaunchArgs &A = cx.A;
-    const int g = A.frame, D = A.S.max_depth, mask = A.tech_mask;
-    const int frames[2] = {g, 3 - g};
-    const float pLi = 1.0f / A.S.emit_area;
-    const Vtx &xD = z[0];
-    const float pcosD = area_from_dir(cosine_pdf(xD.n, unit3(y[1].p - xD.p)), xD.p, y[1]);
-    fast_detail::Eye ze;
-    fast_detail::Light yl;
-    fast_eye(cx, 2, frames, z, nz, cam, mask, ze);
-    fast_light(cx, 2, frames, y, L, ny, nee, mask, pcosD, yl);
-    const float Gd = G2(xD, y[1]);
-    float3 rD[2];
-    float pE[2], pL[2];
-    for (int f = 0; f < 2; ++f) {
-        const Mat m = get_mat(cx, frames[f], xD.mat);
-        rD[f] = rho3(m, z[1], xD, y[1]) * Gd;
-        pE[f] = pdf3(m, z[1], xD, y[1]);
-        pL[f] = pdf3(m, y[1], xD, z[1]);
-    }
-    for (int t = 1; t <= nz; ++t) {
-        if (!(cam & (1u << t))) continue;
-        for (int s = 1; s <= ny && t + s <= D - 2; ++s) {
-            if (!(nee & (1u << s))) continue;
-            float3 fv[2];
-            float P[2];
-            for (int f = 0; f < 2; ++f) {
-                fv[f] = mul3(mul3(ze.E[f][t], rD[f]), yl.L[f][s]);
-                P[f] = pLi * (pE[f] * yl.Py[f][s] * ze.A[f][t] + pL[f] * ze.Pz[f][t] * yl.B[f][s]);
-            }
-            emit_nomotion(cx, pc, root, T_3, t, s, ze.pix[t], fv[0], P[0], fv[1], P[1]);
-        }
-    }
-}
-
-// Running states of fast_eye and fast_light for both frames, advanced one
-// walk vertex at a time (the streaming evaluators below read the walk's
-// vertices where they are needed instead of copying whole walks into
-// thread-local arrays).  Each frame's products, their updates and the
-// power-of-two rescaling (exponent chosen in frame 0, applied to both)
-// follow fast_eye and fast_light step by step.
+// Running states of the eye side (E, Pf, Pz, Sz) and of the light side
+// (Ly, Py, PLy, Sy) for both frames, advanced one walk vertex at a time: the
+// evaluators below read each vertex from the root's slots where it is
+// needed (no thread-local copies of whole walks).  The rescaling exponent
+// of a step is chosen in frame 0 and applied to both frames.
 struct EyeRun {
     float3 rho[2];
     float Pf[2], Pz[2], Sz[2];
@@ -355,13 +211,13 @@ struct LightRun {
     }
 };
 
-// technique (3), the values of fast_t3: the eye-side state advances along
-// t and, for each t with a camera connection, the light-side state is
+// technique (3): all (t, s) paths of one root; the eye-side state advances
+// along t and, for each t with a camera connection, the light-side state is
 // rebuilt along s (the light walk's factors are recomputed for every t
 // rather than stored per vertex).  Vertices come from ld.vtx(slot),
 // ld.eye(m), ld.light(m), ld.nee(m).
 template <class Ld>
-__device__ void fast_t3_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
+__device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
                                uint32_t cam, int ny, uint32_t nee) {
     using namespace chain_detail;
     using namespace fast_detail;
@@ -428,9 +284,9 @@ __device__ void fast_t3_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld 
     }
 }
 
-// technique (1), the values of fast_t1, streaming the eye walk
+// technique (1): paths (camera, z_t .. z_1, x_D, x_L), t = 0 .. nz
 template <class Ld>
-__device__ void fast_t1_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
+__device__ void fast_t1(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
                                uint32_t cam) {
     using namespace chain_detail;
     using namespace fast_detail;
@@ -488,9 +344,9 @@ __device__ void fast_t1_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld 
     }
 }
 
-// technique (2), the values of fast_t2, streaming the light walk
+// technique (2): paths (camera, x_D, y_1 .. y_s, L_s), s = 1 .. ny
 template <class Ld>
-__device__ void fast_t2_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int ny,
+__device__ void fast_t2(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int ny,
                                uint32_t nee) {
     using namespace chain_detail;
     using namespace fast_detail;
@@ -539,90 +395,10 @@ __device__ void fast_t2_stream(Ctx &cx, PathCounts &pc, uint32_t root, const Ld 
     }
 }
 
-// technique (1): paths (camera, z_t .. z_1, x_D, x_L), t = 0 .. nz
-__device__ void fast_t1(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *z, int nz, uint32_t cam,
-                        const Vtx &xL) {
-    using namespace chain_detail;
-    const LaunchArgs &A = cx.A;
-    const DevScene &Sc = A.S;
-    const int g = A.frame, mask = A.tech_mask;
-    const int frames[2] = {g, 3 - g};
-    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
-    const Vtx &xD = z[0];
-    const float3 Le = get_mat(cx, g, xL.mat).em * G2(xD, xL);
-    const Vtx camv = camera_vertex(cx);
-    if (cam & 1u) {                              // t = 0: (camera, x_D, x_L)
-        const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, xD);
-        if (ct.we > 0.f) {
-            const float P = pLi * (((mask & 8) ? ct.pcam : 0.f) + ((mask & 1) ? pD : 0.f));
-            const float3 base = Le * ct.we;
-            emit_nomotion(cx, pc, root, T_1, 0, 0, ct.pix,
-                          mul3(base, rho3(get_mat(cx, frames[0], xD.mat), camv, xD, xL)), P,
-                          mul3(base, rho3(get_mat(cx, frames[1], xD.mat), camv, xD, xL)), P);
-        }
-    }
-    if (nz == 0) return;
-    fast_detail::Eye ze;
-    fast_eye(cx, 2, frames, z, nz, cam, mask, ze);
-    float3 rD[2];
-    float pLL[2];
-    for (int f = 0; f < 2; ++f) {
-        const Mat m = get_mat(cx, frames[f], xD.mat);
-        rD[f] = mul3(rho3(m, z[1], xD, xL), Le);
-        pLL[f] = pdf3(m, xL, xD, z[1]);
-    }
-    for (int t = 1; t <= nz; ++t) {
-        if (!(cam & (1u << t))) continue;
-        float3 fv[2];
-        float P[2];
-        for (int f = 0; f < 2; ++f) {
-            fv[f] = mul3(ze.E[f][t], rD[f]);
-            P[f] = pLi * (ze.A[f][t] + ((mask & 1) ? pD * ze.Pz[f][t] * pLL[f] : 0.f));
-        }
-        emit_nomotion(cx, pc, root, T_1, t, 0, ze.pix[t], fv[0], P[0], fv[1], P[1]);
-    }
-}
-
-// technique (2): paths (camera, x_D, y_1 .. y_s, L_s), s = 1 .. ny
-__device__ void fast_t2(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *y, const Vtx *L, int ny,
-                        uint32_t nee) {
-    using namespace chain_detail;
-    const LaunchArgs &A = cx.A;
-    const DevScene &Sc = A.S;
-    const int g = A.frame, mask = A.tech_mask;
-    const int frames[2] = {g, 3 - g};
-    const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
-    const Vtx &xD = y[0];
-    const Vtx camv = camera_vertex(cx);
-    const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, xD);
-    if (ct.we <= 0.f) return;
-    fast_detail::Light yl;
-    // x_D is technique (2) here: no technique-(3) term at x_D
-    fast_light(cx, 2, frames, y, L, ny, nee, mask, 0.f, yl);
-    const float Gd = G2(xD, y[1]);
-    const float a = ((mask & 8) ? ct.pcam : 0.f) + ((mask & 2) ? pD : 0.f);
-    float3 rD[2];
-    float pEC[2];
-    for (int f = 0; f < 2; ++f) {
-        const Mat m = get_mat(cx, frames[f], xD.mat);
-        rD[f] = rho3(m, camv, xD, y[1]) * (ct.we * Gd);
-        pEC[f] = pdf3(m, camv, xD, y[1]);
-    }
-    for (int s = 1; s <= ny; ++s) {
-        if (!(nee & (1u << s))) continue;
-        float3 fv[2];
-        float P[2];
-        for (int f = 0; f < 2; ++f) {
-            fv[f] = mul3(rD[f], yl.L[f][s]);
-            P[f] = pLi * (a * pEC[f] * yl.Py[f][s] + yl.B[f][s]);
-        }
-        emit_nomotion(cx, pc, root, T_2, 0, s, ct.pix, fv[0], P[0], fv[1], P[1]);
-    }
-}
-
 // path tracing: paths (camera, x_1 .. x_j, L_j); residual (technique (7),
 // both frames, static paths skipped) or primal (one frame, path tracing only)
-__device__ void fast_pt(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *x, const Vtx *L, int len,
+template <class Ld>
+__device__ void fast_pt(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int len,
                         uint32_t nee, int tech) {
     using namespace chain_detail;
     const LaunchArgs &A = cx.A;
@@ -634,37 +410,37 @@ __device__ void fast_pt(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *x, co
     const int frames[2] = {g, 3 - g};
     const float pD = 1.0f / Sc.dyn_area, pLi = 1.0f / Sc.emit_area;
     const Vtx camv = camera_vertex(cx);
-    const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, x[1]);
+    Vtx xj = ld.vtx(0), xp = camv;      // x_1 is in slot 0, x_m (m >= 2) in light slot m - 1
+    const fast_detail::CamTerm ct = fast_detail::cam_term(Sc, camv, xj);
     if (ct.we <= 0.f) return;
     if (!res) {                    // the camera ray sees an emitter: (camera, x_1)
-        const float3 em = get_mat(cx, g, x[1].mat).em;
+        const float3 em = get_mat(cx, g, xj.mat).em;
         if (!zero3(em)) emit_nomotion(cx, pc, root, tech, 0, 2, ct.pix, em * ct.we, ct.pcam, em, 0.f);
     }
-    const bool d1 = is_dyn(cx, x[1]);
+    const bool d1 = is_dyn(cx, xj);
     float3 R[2] = {f3(ct.we, ct.we, ct.we), f3(ct.we, ct.we, ct.we)};
     float PE[2] = {1.f, 1.f}, PL[2] = {1.f, 1.f}, S3[2] = {0.f, 0.f};
     bool any_dyn = false;
     for (int j = 1; j <= len; ++j) {
-        const Vtx &xj = x[j];
-        const Vtx &xp = (j == 1) ? camv : x[j - 1];
         const bool dj = is_dyn(cx, xj);
         any_dyn = any_dyn || dj;
         if ((nee & (1u << j)) && (!res || any_dyn)) {
-            const float GL = G2(xj, L[j]);
+            const Vtx Lj = ld.nee(j);
+            const float GL = G2(xj, Lj);
             float3 fv[2];
             float P[2] = {0.f, 0.f};
             for (int f = 0; f < nf; ++f) {
                 const Mat m = get_mat(cx, frames[f], xj.mat);
-                fv[f] = mul3(mul3(R[f], rho3(m, xp, xj, L[j])) * GL, get_mat(cx, frames[f], L[j].mat).em);
+                fv[f] = mul3(mul3(R[f], rho3(m, xp, xj, Lj)) * GL, get_mat(cx, frames[f], Lj.mat).em);
                 float p = ((mask & 8) ? ct.pcam * PE[f] : 0.f) +
                           ((mask & 2) && d1 && j >= 2 ? pD * PE[f] : 0.f) + ((mask & 4) ? pD * S3[f] : 0.f);
-                if ((mask & 1) && dj) p += pD * (j == 1 ? 1.f : PL[f] * pdf3(m, L[j], xj, xp));
+                if ((mask & 1) && dj) p += pD * (j == 1 ? 1.f : PL[f] * pdf3(m, Lj, xj, xp));
                 P[f] = pLi * p;
             }
             emit_nomotion(cx, pc, root, tech, 0, j + 2, ct.pix, fv[0], P[0], fv[1], P[1]);
         }
         if (j < len) {
-            const Vtx &xn = x[j + 1];
+            const Vtx xn = ld.light(j);
             for (int f = 0; f < nf; ++f) {
                 const Mat m = get_mat(cx, frames[f], xj.mat);
                 const float pE = pdf3(m, xp, xj, xn);
@@ -687,6 +463,8 @@ __device__ void fast_pt(Ctx &cx, PathCounts &pc, uint32_t root, const Vtx *x, co
                     R[f] = R[f] * sc; PE[f] *= sc; PL[f] *= sc; S3[f] *= sc;
                 }
             }
+            xp = xj;
+            xj = xn;
         }
     }
 }

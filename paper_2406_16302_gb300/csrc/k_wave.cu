@@ -675,7 +675,6 @@ __global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ Launc
     PathCounts pc{0, 0, 0};
     unsigned int roots = 0;
     const int D = A.S.max_depth;
-    Vtx zv[kMaxDepth + 1], yv[kMaxDepth + 1], Lv[kMaxDepth + 1];
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         ++roots;
         const uint32_t root = A.root_begin + r;
@@ -690,11 +689,7 @@ __global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ Launc
                     any_dyn = W.prim[(size_t)(j == 1 ? 0 : slot_light(D, j - 1)) * W.R + r] >= A.S.n_static;
                 if (!any_dyn) continue;
             }
-            for (int j = 1; j <= len; ++j) {
-                yv[j] = load_vtx(c, W, j == 1 ? 0 : slot_light(D, j - 1), r);
-                if (nee & (1u << j)) Lv[j] = load_vtx(c, W, slot_nee(D, j), r);
-            }
-            fast_pt(c, pc, root, yv, Lv, len, nee, A.residual ? T_7 : T_PT);
+            fast_pt(c, pc, root, SlotLoader{c, W, r, D}, len, nee, A.residual ? T_7 : T_PT);
             continue;
         }
         if ((T == T_1 || T == T_2) && !(W.flags[r] & RF_ROOT_OK)) continue;
@@ -702,25 +697,12 @@ __global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ Launc
         const int ny = (T == T_1) ? 0 : W.len_light[r];
         if (T == T_3 && (nz == 0 || ny == 0)) continue;
         if constexpr (T == T_3) {
-            fast_t3_stream(c, pc, root, SlotLoader{c, W, r, D}, nz, cam, ny, nee);
-            continue;
+            fast_t3(c, pc, root, SlotLoader{c, W, r, D}, nz, cam, ny, nee);
         } else if constexpr (T == T_1) {
-            fast_t1_stream(c, pc, root, SlotLoader{c, W, r, D}, nz, cam);
-            continue;
-        } else if constexpr (T == T_2) {
-            fast_t2_stream(c, pc, root, SlotLoader{c, W, r, D}, ny, nee);
-            continue;
+            fast_t1(c, pc, root, SlotLoader{c, W, r, D}, nz, cam);
+        } else {
+            fast_t2(c, pc, root, SlotLoader{c, W, r, D}, ny, nee);
         }
-        zv[0] = load_vtx(c, W, 0, r);
-        for (int m = 1; m <= nz; ++m) zv[m] = load_vtx(c, W, slot_eye(D, m), r);
-        yv[0] = zv[0];
-        for (int m = 1; m <= ny; ++m) {
-            yv[m] = load_vtx(c, W, slot_light(D, m), r);
-            if (nee & (1u << m)) Lv[m] = load_vtx(c, W, slot_nee(D, m), r);
-        }
-        if (T == T_1) fast_t1(c, pc, root, zv, nz, cam, load_vtx(c, W, 1, r));
-        else if (T == T_2) fast_t2(c, pc, root, yv, Lv, ny, nee);
-        else fast_t3(c, pc, root, zv, nz, cam, yv, Lv, ny, nee);
     }
     if (A.stats) {
         add_stat(A.stats, ST_ROOTS, roots);
