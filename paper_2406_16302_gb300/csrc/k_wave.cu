@@ -668,7 +668,9 @@ __global__ void __launch_bounds__(128) k_enum(const __grid_constant__ LaunchArgs
 // edits without motion, and the primal: every base path of a root from
 // running products along its walks (chain_fast.cuh), O(1) work per path
 template <int T>
-__global__ void __launch_bounds__(128) k_eval_fast(const __grid_constant__ LaunchArgs A) {
+// (register budgets: technique (3)'s nested walks at 4 blocks per SM, the
+// others at 5)
+__global__ void __launch_bounds__(128, T == T_3 ? 4 : 5) k_eval_fast(const __grid_constant__ LaunchArgs A) {
     const uint32_t n = A.root_end - A.root_begin;
     const WaveBuf &W = A.W;
     Ctx c(A, nullptr);
