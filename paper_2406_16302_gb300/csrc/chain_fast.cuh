@@ -211,14 +211,17 @@ struct LightRun {
     }
 };
 
-// technique (3): all (t, s) paths of one root; the eye-side state advances
-// along t and, for each t with a camera connection, the light-side state is
-// rebuilt along s (the light walk's factors are recomputed for every t
-// rather than stored per vertex).  Vertices come from ld.vtx(slot),
-// ld.eye(m), ld.light(m), ld.nee(m).
+// technique (3): all (t, s) paths of one root.  The light side is walked
+// once: for each s with a next-event vertex its Ly(s), Py(s), B(s) of both
+// frames (10 values) go to the thread's column of `sl` (shared memory,
+// entry e of s at sl[((s - 1) * 10 + e) * stride]); then the eye-side state
+// advances along t and pairs with them.  Vertices come from ld.vtx(slot),
+// ld.eye(m), ld.light(m), ld.nee(m).  s never exceeds D - 3 (t >= 1).
+constexpr int kT3LightSlots = kMaxDepth - 3;
+
 template <class Ld>
 __device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, int nz,
-                               uint32_t cam, int ny, uint32_t nee) {
+                        uint32_t cam, int ny, uint32_t nee, float *sl, int stride) {
     using namespace chain_detail;
     using namespace fast_detail;
     const LaunchArgs &A = cx.A;
@@ -228,8 +231,36 @@ __device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, in
     const float pLi = 1.0f / Sc.emit_area, pD = 1.0f / Sc.dyn_area;
     const Vtx xD = ld.vtx(0);
     const Vtx y1 = ld.light(1);
-    Vtx zm = ld.eye(1), zp = xD;
     const float pcosD = area_from_dir(cosine_pdf(xD.n, unit3(y1.p - xD.p)), xD.p, y1);
+    const int smax = ny < D - 3 ? ny : D - 3;
+    {
+        LightRun lr;
+        lr.init();
+        Vtx ym = y1, yp = xD;
+        for (int s = 1; s <= smax; ++s) {
+            const bool dyny = is_dyn(cx, ym);
+            if (nee & (1u << s)) {
+                float3 Ly[2];
+                float Pyt[2], B[2];
+                lr.nee_values(cx, frames, mask, pD, pcosD, ym, yp, ld.nee(s), dyny, Ly, Pyt, B);
+                float *e = sl + (size_t)(s - 1) * 10 * stride;
+                for (int f = 0; f < 2; ++f) {
+                    e[(5 * f + 0) * stride] = Ly[f].x;
+                    e[(5 * f + 1) * stride] = Ly[f].y;
+                    e[(5 * f + 2) * stride] = Ly[f].z;
+                    e[(5 * f + 3) * stride] = Pyt[f];
+                    e[(5 * f + 4) * stride] = B[f];
+                }
+            }
+            if (s < smax) {
+                const Vtx yn = ld.light(s + 1);
+                lr.advance(cx, frames, ym, yp, yn, dyny);
+                yp = ym;
+                ym = yn;
+            }
+        }
+    }
+    Vtx zm = ld.eye(1), zp = xD;
     const float Gd = G2(xD, y1);
     float3 rD[2];
     float pE[2], pL[2];
@@ -250,29 +281,19 @@ __device__ void fast_t3(Ctx &cx, PathCounts &pc, uint32_t root, const Ld &ld, in
             float3 E[2];
             float At[2], Pzt[2];
             er.cam_values(cx, frames, mask, pD, ct, camv, zm, zp, G, dynz, E, At, Pzt);
-            LightRun lr;
-            lr.init();
-            Vtx ym = y1, yp = xD;
             for (int s = 1; s <= ny && t + s <= D - 2; ++s) {
-                const bool dyny = is_dyn(cx, ym);
-                if (nee & (1u << s)) {
-                    float3 Ly[2];
-                    float Pyt[2], B[2];
-                    lr.nee_values(cx, frames, mask, pD, pcosD, ym, yp, ld.nee(s), dyny, Ly, Pyt, B);
-                    float3 fv[2];
-                    float P[2];
-                    for (int f = 0; f < 2; ++f) {
-                        fv[f] = mul3(mul3(E[f], rD[f]), Ly[f]);
-                        P[f] = pLi * (pE[f] * Pyt[f] * At[f] + pL[f] * Pzt[f] * B[f]);
-                    }
-                    emit_nomotion(cx, pc, root, T_3, t, s, ct.pix, fv[0], P[0], fv[1], P[1]);
+                if (!(nee & (1u << s))) continue;
+                const float *e = sl + (size_t)(s - 1) * 10 * stride;
+                float3 fv[2];
+                float P[2];
+                for (int f = 0; f < 2; ++f) {
+                    const float3 Ly = f3(e[(5 * f + 0) * stride], e[(5 * f + 1) * stride],
+                                         e[(5 * f + 2) * stride]);
+                    const float Pyt = e[(5 * f + 3) * stride], B = e[(5 * f + 4) * stride];
+                    fv[f] = mul3(mul3(E[f], rD[f]), Ly);
+                    P[f] = pLi * (pE[f] * Pyt * At[f] + pL[f] * Pzt[f] * B);
                 }
-                if (s < ny && t + s + 1 <= D - 2) {
-                    const Vtx yn = ld.light(s + 1);
-                    lr.advance(cx, frames, ym, yp, yn, dyny);
-                    yp = ym;
-                    ym = yn;
-                }
+                emit_nomotion(cx, pc, root, T_3, t, s, ct.pix, fv[0], P[0], fv[1], P[1]);
             }
         }
         if (t < nz) {

@@ -671,6 +671,8 @@ template <int T>
 // (register budgets: technique (3)'s nested walks at 4 blocks per SM, the
 // others at 5)
 __global__ void __launch_bounds__(128, T == T_3 ? 4 : 5) k_eval_fast(const __grid_constant__ LaunchArgs A) {
+    // technique (3): each thread's light-side values per s (fast_t3)
+    __shared__ float s_light[T == T_3 ? kT3LightSlots * 10 * 128 : 1];
     const uint32_t n = A.root_end - A.root_begin;
     const WaveBuf &W = A.W;
     Ctx c(A, nullptr);
@@ -699,7 +701,8 @@ __global__ void __launch_bounds__(128, T == T_3 ? 4 : 5) k_eval_fast(const __gri
         const int ny = (T == T_1) ? 0 : W.len_light[r];
         if (T == T_3 && (nz == 0 || ny == 0)) continue;
         if constexpr (T == T_3) {
-            fast_t3(c, pc, root, SlotLoader{c, W, r, D}, nz, cam, ny, nee);
+            fast_t3(c, pc, root, SlotLoader{c, W, r, D}, nz, cam, ny, nee, s_light + threadIdx.x,
+                    blockDim.x);
         } else if constexpr (T == T_1) {
             fast_t1(c, pc, root, SlotLoader{c, W, r, D}, nz, cam);
         } else {
