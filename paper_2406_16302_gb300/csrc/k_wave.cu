@@ -863,8 +863,10 @@ __device__ void map_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t t
 
 }  // namespace
 
-// stage C1: one thread per mapping task (map_task)
-__global__ void __launch_bounds__(kBlock) k_map_a(const __grid_constant__ LaunchArgs A) {
+// stage C1: one thread per mapping task (map_task).  Latency-bound (long
+// dependent loads, divergent lanes): 8 blocks per SM at 64 registers run it
+// faster than 4 blocks at 128 despite the spills
+__global__ void __launch_bounds__(kBlock, 8) k_map_a(const __grid_constant__ LaunchArgs A) {
     __shared__ int s_stack[kStackDepth * kBlock];
     Ctx c(A, s_stack + threadIdx.x);
     PathCounts pc{0, 0, 0};
