@@ -50,8 +50,8 @@ BYTES_PER_RAY = {"k_trace_closest": 32 + 28, "k_trace_shadow": 40}
 # (profiles/k_trace_closest_box_blob_material_256.md): dram read + write bytes
 # per traced ray, valid while the kernel's sources hash to KERNEL_SOURCES_SHA
 TRAFFIC_CAPTURE = {"kernel": "k_trace_closest", "workload": "box_blob_material_256",
-                   "dram_bytes_per_ray": (2125.964544e6 + 446.330112e6) / 57820270.0,
-                   "sources_sha": "86da15c680a0e777"}
+                   "dram_bytes_per_ray": (2126.010368e6 + 445.262080e6) / 57820270.0,
+                   "sources_sha": "ca6e970db6ab6a9a"}
 KERNEL_SOURCES = ["rp_device.cuh", "k_wave.cu", "rp_internal.h", "rp_wave.h"]
 
 
@@ -485,7 +485,50 @@ def cpu_baseline(scene, edit, spp, target_s=15.0):
     dt = (time.perf_counter() - t0) / reps
     return {"value": R * 8 / dt, "unit": "residual samples/s", "cores": 1, "kind": "oracle",
             "sample": f"roots [0, {R}) of each of the 4 techniques in both frames "
-                      f"({R * 8} residual samples) per run, {reps} runs, single-threaded FP64 C"}
+                      f"({R * 8} residual samples) per run, {reps} runs, single-threaded FP64 C",
+            "roots": R, "n_roots": o.n_roots(spp)}
+
+
+def _oracle_worker(name, spp, a, R, seed, barrier, results):
+    """One process of the multi-core oracle timing: roots [a, a+R) of every
+    technique in both frames, started together with the others."""
+    import oracle
+    scene, edit, _ = workload(name)
+    o = oracle.Oracle(scene, edit)
+    o.render_residual(spp, seed, a, a + min(R, 16))          # page in, build the BVH
+    barrier.wait()
+    t0 = time.perf_counter()
+    o.render_residual(spp, seed, a, a + R)
+    results.put(time.perf_counter() - t0)
+
+
+def cpu_baseline_multicore(name, spp, R, n_roots, cores=None):
+    """The single-threaded oracle run in one spawned process per host core on
+    disjoint root ranges of R roots each; value = all roots / the wall time
+    from a common start to the last process's end."""
+    import multiprocessing as mp
+    if cores is None:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = max(1, min(cores, n_roots // max(R, 1)))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores + 1)
+    results = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(name, spp, i * R, R, 7 + i, barrier, results), daemon=True)
+             for i in range(cores)]
+    for p in procs:
+        p.start()
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    per = [results.get(timeout=600) for _ in procs]
+    wall = time.perf_counter() - t0
+    for p in procs:
+        p.join()
+    return {"value": cores * R * 8 / wall, "unit": "residual samples/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{cores} processes, each roots [{R}i, {R}(i+1)) of every technique in both "
+                      f"frames ({cores * R * 8} residual samples), wall {wall:.2f} s "
+                      f"(per process {min(per):.2f}-{max(per):.2f} s)"}
 
 
 def run_reference(args):
@@ -687,6 +730,8 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(scene, edit, spp)
+        cpu["multi_core"] = cpu_baseline_multicore(args.workload, spp, cpu["roots"],
+                                                   cpu["n_roots"])
     et_mse = None
     if not args.no_mse and ws == 1:
         et_mse = equal_time_mse(rp, sc, ed, scene, spp)
@@ -703,7 +748,10 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)",
                    "per_kernel": per_kernel,
                    "rays_per_step": work["rays_closest"] + work["rays_shadow"],
-                   "paths_per_step": work["paths"]},
+                   "paths_per_step": work["paths"],
+                   # splatted base paths per pixel (the paper's spp convention, Sec. 6)
+                   "spp_equivalent": work["paths"] / (scene.camera.width * scene.camera.height)},
+        "root_samples_per_s": value,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "equal_time_mse": et_mse,
         "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clock,
     }

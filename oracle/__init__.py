@@ -89,6 +89,8 @@ def lib():
         L.oracle_mlp_forward.argtypes = [P, P, C.c_int, P]
         L.oracle_mlp_loss_grad.restype = C.c_double
         L.oracle_mlp_loss_grad.argtypes = [P, P, P, P, C.c_int, P]
+        L.oracle_mis_terms.restype = C.c_int
+        L.oracle_mis_terms.argtypes = [P, C.c_int, C.c_int, P, P, C.c_int, P, P, C.c_int]
         assert L.oracle_record_size() == RECORD_DTYPE.itemsize, "record layout mismatch"
     return _lib
 
@@ -309,6 +311,22 @@ class Oracle:
         b1 = np.zeros(n); b2 = np.zeros(n)
         lib().oracle_closest_hit(self.h, frame, n, _p(o), _p(d), _p(t), _p(prim), _p(b1), _p(b2))
         return t, prim, b1, b2
+
+    def mis_terms(self, frame, prims, bary, tech_mask=MASK_SEVEN):
+        """The balance-heuristic denominator's terms (technique, per-root area
+        density) of the path camera -> (prims[i], bary[i]) ... in `frame`, the
+        last vertex on an emitter (Sec. 4.3; ghost terms Sec. 4.2)."""
+        prims = np.ascontiguousarray(prims, dtype=np.int32)
+        bary = np.ascontiguousarray(bary, dtype=np.float64).reshape(-1, 2)
+        k = len(prims) + 1
+        cap = 64
+        tech = np.zeros(cap, dtype=np.int32)
+        dens = np.zeros(cap)
+        n = lib().oracle_mis_terms(self.h, frame, k, _p(prims), _p(bary), tech_mask, _p(tech),
+                                   _p(dens), cap)
+        if n < 0:
+            raise ValueError("bad path")
+        return tech[:min(n, cap)].copy(), dens[:min(n, cap)].copy()
 
     def check_mapping(self, tech, frame, spp, seed, root_begin, root_end):
         out = np.zeros(6)

@@ -718,19 +718,46 @@ static double ghost_ray_pdf(double pD, vec3 o, const gcross *c, const vtx *x1) {
     return pD * dot(og, og) / cg * c1 / dot(o1, o1);
 }
 
+/* the terms of the balance-heuristic denominator, summed in order and, when
+ * terms != NULL, recorded one by one (technique id and density) */
+typedef struct {
+    double sum;
+    int n, cap;
+    double *terms;
+    int *tech;
+} termacc;
+
+static void add_term(termacc *a, int tech, double p) {
+    a->sum += p;
+    if (a->terms && a->n < a->cap) {
+        a->terms[a->n] = p;
+        a->tech[a->n] = tech;
+    }
+    a->n++;
+}
+
 /* sum over the enabled techniques that produce x of their per-root densities */
+static double mis_terms(const oscene *s, int g, const vtx *x, int k, techmask tm, termacc *acc);
+
 static double mis_denominator(const oscene *s, int g, const vtx *x, int k, techmask tm) {
+    termacc acc = {0.0, 0, 0, NULL, NULL};
+    return mis_terms(s, g, x, k, tm, &acc);
+}
+
+static double mis_terms(const oscene *s, int g, const vtx *x, int k, techmask tm, termacc *acc) {
     double pE[16], pL[16];
     double pD = 1.0 / s->dyn_area, pLi = 1.0 / s->emit_area;
-    if (k == 2) return tm.t7 ? pdf_camera_area(s, &x[1]) : 0.0;
+    if (k == 2) {
+        if (tm.t7) add_term(acc, 7, pdf_camera_area(s, &x[1]));
+        return acc->sum;
+    }
     pE[1] = pdf_camera_area(s, &x[1]);
     for (int j = 2; j <= k - 2; ++j) pE[j] = step_pdf(x, j - 2, j - 1, j);
     for (int j = 1; j <= k - 3; ++j) pL[j] = step_pdf(x, j + 2, j + 1, j);
-    double sum = 0.0;
     if (tm.t7) {
         double p = pLi;
         for (int j = 1; j <= k - 2; ++j) p *= pE[j];
-        sum += p;
+        add_term(acc, 7, p);
     }
     for (int i = 1; i <= k - 2; ++i) {
         if (!x[i].dyn) continue;
@@ -738,19 +765,19 @@ static double mis_denominator(const oscene *s, int g, const vtx *x, int k, techm
             if (!tm.t1) continue;
             double p = pD * pLi;
             for (int j = 1; j <= k - 3; ++j) p *= pL[j];
-            sum += p;
+            add_term(acc, 1, p);
         } else if (i == 1) {                  /* (2) dynamic from sensor */
             if (!tm.t2) continue;
             double p = pD * pLi;
             for (int j = 2; j <= k - 2; ++j) p *= pE[j];
-            sum += p;
+            add_term(acc, 2, p);
         } else {                              /* (3) dynamic two ends */
             if (!tm.t3) continue;
             vec3 w = normalize(sub(x[i + 1].p, x[i].p));
             double p = pD * pLi * area_from_dir(cosine_pdf(x[i].n, w), x[i].p, &x[i + 1]);
             for (int j = i + 2; j <= k - 2; ++j) p *= pE[j];
             for (int j = 1; j <= i - 1; ++j) p *= pL[j];
-            sum += p;
+            add_term(acc, 3, p);
         }
     }
     /* (4)-(6): one term per ghost crossing of an edge; (5) on the first edge,
@@ -780,11 +807,11 @@ static double mis_denominator(const oscene *s, int g, const vtx *x, int k, techm
                     for (int m = 1; m <= j - 1; ++m) p *= pL[m];
                     for (int m = j + 2; m <= k - 2; ++m) p *= pE[m];
                 }
-                sum += p;
+                add_term(acc, kind, p);
             }
         }
     }
-    return sum;
+    return acc->sum;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1828,6 +1855,26 @@ static techmask mask_from(int m) {
     techmask t = {(m >> 0) & 1, (m >> 1) & 1, (m >> 2) & 1, (m >> 3) & 1,
                   (m >> 4) & 1, (m >> 5) & 1, (m >> 6) & 1};
     return t;
+}
+
+/* the denominator's terms for the frame-g path x_0 = camera, x_i = the point
+ * (bary[2(i-1)], bary[2(i-1)+1]) on prim[i-1] for i = 1..k-1, x_{k-1} on an
+ * emitter (Sec. 4.3; ghost terms Sec. 4.2): up to cap (technique, density)
+ * pairs are written; returns the number of terms, -1 on a bad argument */
+int oracle_mis_terms(void *h, int g, int k, const int *prim, const double *bary, int tech_mask,
+                     int *tech, double *dens, int cap) {
+    const oscene *s = (const oscene *)h;
+    if (!s || k < 2 || k > 15 || (g != 1 && g != 2)) return -1;
+    vtx x[16];
+    x[0] = camera_vertex(s);
+    for (int i = 1; i < k; ++i) {
+        if (prim[i - 1] < 0 || prim[i - 1] >= s->n_static + s->n_dyn) return -1;
+        if (prim[i - 1] >= s->n_static && !s->has_edit) return -1;
+        x[i] = make_vertex(s, g, prim[i - 1], bary[2 * (i - 1)], bary[2 * (i - 1) + 1]);
+    }
+    termacc acc = {0.0, 0, cap, dens, tech};
+    mis_terms(s, g, x, k, mask_from(tech_mask), &acc);
+    return acc.n;
 }
 
 /* run roots [r0, r1) of one technique in one frame */

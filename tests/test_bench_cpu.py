@@ -53,3 +53,11 @@ def test_gpu_arm_refuses_without_a_device():
     r = _run(["--steps", "1", "--warmup", "0"], timeout=300)
     assert r.returncode != 0
     assert "CUDA device" in (r.stderr + r.stdout)
+
+
+def test_multicore_oracle_timing_uses_disjoint_ranges():
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.cpu_baseline_multicore("box_sphere_motion_64", 16, 64, 1 << 16, cores=2)
+    assert d["kind"] == "oracle" and d["cores"] == 2 and d["value"] > 0
+    assert "1024 residual samples" in d["sample"]
