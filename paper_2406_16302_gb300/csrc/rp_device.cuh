@@ -525,7 +525,7 @@ static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin,
                 --sp;
                 node = stack[sp * kBlock];
             }
-            if (pa >= 0 && __all_sync(__activemask(), pa >= 0)) break;
+            if (pa >= 0 && (any || __all_sync(__activemask(), pa >= 0))) break;
         }
         if (pa < 0) break;           // nothing pending and nothing left to visit
         for (int slot = 0; slot < 2; ++slot) {
