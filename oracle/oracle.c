@@ -29,7 +29,7 @@
  *     density (not in the paper; an integer network evaluated exactly), and
  *     the float network's loss and gradient used to train it.
  *
- * Readings of the paper where it is silent (each listed in the design doc):
+ * Readings of the paper where it is silent, ambiguous or garbled:
  *   R1 area measure everywhere: |J| of object transform and of reconnection
  *      is 1; a replayed vertex contributes the ratio of its area sampling
  *      densities in the two frames.

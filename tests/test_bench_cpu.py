@@ -1,6 +1,6 @@
 """The benchmark's contract on the host: the reference arm (the oracle,
-timed on the host cores) prints one JSON line with the fields the driver
-reads; ranks other than 0 print nothing; the GPU arm refuses to run without
+timed on the host cores) prints one JSON line with every field of the output
+contract; ranks other than 0 print nothing; the GPU arm refuses to run without
 a CUDA device instead of falling back to the CPU."""
 import json
 import os
