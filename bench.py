@@ -50,8 +50,8 @@ BYTES_PER_RAY = {"k_trace_closest": 32 + 28, "k_trace_shadow": 40}
 # (profiles/k_trace_closest_box_blob_material_256.md): dram read + write bytes
 # per traced ray, valid while the kernel's sources hash to KERNEL_SOURCES_SHA
 TRAFFIC_CAPTURE = {"kernel": "k_trace_closest", "workload": "box_blob_material_256",
-                   "dram_bytes_per_ray": (2125.720576e6 + 445.925376e6) / 57820270.0,
-                   "sources_sha": "6ea01c96b805ee14"}
+                   "dram_bytes_per_ray": (2126.010368e6 + 445.262080e6) / 57820270.0,
+                   "sources_sha": "ca6e970db6ab6a9a"}
 KERNEL_SOURCES = ["rp_device.cuh", "k_wave.cu", "rp_internal.h", "rp_wave.h"]
 
 

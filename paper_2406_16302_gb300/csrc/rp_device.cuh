@@ -479,89 +479,69 @@ static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin,
     const float3 oid = f3(o.x * id.x, o.y * id.y, o.z * id.z);
     int sp = 0;
     int node = 0;
-    // leaves whose boxes were hit wait in two slots, each a node's leaf
-    // children as (node << 2 | side mask), while the lane keeps descending;
-    // the warp tests triangles once every lane holds one (postponed leaves,
-    // Aila and Laine 2009), so lanes run the triangle loop together
-    int pa = -1, pb = -1;
     bool found = false;
     for (;;) {
-        while (node >= 0 && pb < 0) {
-            ++cnt.nodes;
-            const float4 na = __ldg(&B.nodes[4 * node + 0]);
-            const float4 nb = __ldg(&B.nodes[4 * node + 1]);
-            const float4 nc = __ldg(&B.nodes[4 * node + 2]);
-            const float4 nd = __ldg(&B.nodes[4 * node + 3]);
-            const int c0 = __float_as_int(nd.x), c1 = __float_as_int(nd.y);
-            float t0, t1;
-            bool h0 = box_hit(na.x, na.y, na.z, na.w, nc.x, nc.y, id, oid, tmin, tmax, t0);
-            bool h1 = box_hit(nb.x, nb.y, nb.z, nb.w, nc.z, nc.w, id, oid, tmin, tmax, t1);
-            const int lm = ((h0 && c0 < 0) ? 1 : 0) | ((h1 && c1 < 0) ? 2 : 0);
-            if (lm) {
-                if (pa < 0) pa = (node << 2) | lm;
-                else pb = (node << 2) | lm;
+        ++cnt.nodes;
+        const float4 na = __ldg(&B.nodes[4 * node + 0]);
+        const float4 nb = __ldg(&B.nodes[4 * node + 1]);
+        const float4 nc = __ldg(&B.nodes[4 * node + 2]);
+        const float4 nd = __ldg(&B.nodes[4 * node + 3]);
+        const int c0 = __float_as_int(nd.x), c1 = __float_as_int(nd.y);
+        float t0, t1;
+        bool h0 = box_hit(na.x, na.y, na.z, na.w, nc.x, nc.y, id, oid, tmin, tmax, t0);
+        bool h1 = box_hit(nb.x, nb.y, nb.z, nb.w, nc.z, nc.w, id, oid, tmin, tmax, t1);
+        for (int side = 0; side < 2; ++side) {
+            const bool hs = side ? h1 : h0;
+            const int cs = side ? c1 : c0;
+            if (!hs || cs >= 0) continue;
+            const int first = ~cs;
+            const int count = __float_as_int(side ? nd.w : nd.z);
+            for (int i = first; i < first + count; ++i) {
+                ++cnt.tris;
+                const float4 v0 = __ldg(&B.tris[3 * i + 0]);
+                const int gid = __float_as_int(v0.w) + id_add;
+                if (gid == ex0 || gid == ex1) continue;
+                if ((unsigned)(gid - skip_lo) < (unsigned)skip_n &&
+                    (!skip_bits ||
+                     ((__ldg(&skip_bits[(unsigned)(gid - skip_lo) >> 5]) >> ((gid - skip_lo) & 31)) & 1u)))
+                    continue;
+                const float4 v1 = __ldg(&B.tris[3 * i + 1]);
+                const float4 v2 = __ldg(&B.tris[3 * i + 2]);
+                float tt, bb1, bb2;
+                if (tri_hit(w, o, xyz(v0), xyz(v1), xyz(v2), tmin, tmax, tt, bb1, bb2)) {
+                    tmax = tt;
+                    h.t = tt;
+                    h.b1 = bb1;
+                    h.b2 = bb2;
+                    h.prim = gid;
+                    found = true;
+                    if (any) return true;
+                }
             }
-            const bool g0 = h0 && c0 >= 0, g1 = h1 && c1 >= 0;
-            if (g0 && g1) {
-                int nearc = c0, farc = c1;
-                if (t1 < t0) {
-                    nearc = c1;
-                    farc = c0;
-                }
-                if (sp < kStackDepth) {
-                    stack[sp * kBlock] = farc;
-                    ++sp;
-                } else {
-                    *overflow = 1;
-                }
-                node = nearc;
-            } else if (g0) {
-                node = c0;
-            } else if (g1) {
-                node = c1;
-            } else if (sp == 0) {
-                node = -1;
+        }
+        const bool g0 = h0 && c0 >= 0, g1 = h1 && c1 >= 0;
+        if (g0 && g1) {
+            int nearc = c0, farc = c1;
+            if (t1 < t0) {
+                nearc = c1;
+                farc = c0;
+            }
+            if (sp < kStackDepth) {
+                stack[sp * kBlock] = farc;
+                ++sp;
             } else {
-                --sp;
-                node = stack[sp * kBlock];
+                *overflow = 1;
             }
-            if (pa >= 0 && (any || __all_sync(__activemask(), pa >= 0))) break;
+            node = nearc;
+        } else if (g0) {
+            node = c0;
+        } else if (g1) {
+            node = c1;
+        } else {
+            if (sp == 0) break;
+            --sp;
+            node = stack[sp * kBlock];
         }
-        if (pa < 0) break;           // nothing pending and nothing left to visit
-        for (int slot = 0; slot < 2; ++slot) {
-            const int e = slot ? pb : pa;
-            if (e < 0) continue;
-            const float4 nd = __ldg(&B.nodes[4 * (e >> 2) + 3]);
-            for (int side = 0; side < 2; ++side) {
-                if (!((e >> side) & 1)) continue;
-                const int first = ~__float_as_int(side ? nd.y : nd.x);
-                const int count = __float_as_int(side ? nd.w : nd.z);
-                for (int i = first; i < first + count; ++i) {
-                    ++cnt.tris;
-                    const float4 v0 = __ldg(&B.tris[3 * i + 0]);
-                    const int gid = __float_as_int(v0.w) + id_add;
-                    if (gid == ex0 || gid == ex1) continue;
-                    if ((unsigned)(gid - skip_lo) < (unsigned)skip_n &&
-                        (!skip_bits ||
-                         ((__ldg(&skip_bits[(unsigned)(gid - skip_lo) >> 5]) >> ((gid - skip_lo) & 31)) &
-                          1u)))
-                        continue;
-                    const float4 v1 = __ldg(&B.tris[3 * i + 1]);
-                    const float4 v2 = __ldg(&B.tris[3 * i + 2]);
-                    float tt, bb1, bb2;
-                    if (tri_hit(w, o, xyz(v0), xyz(v1), xyz(v2), tmin, tmax, tt, bb1, bb2)) {
-                        tmax = tt;
-                        h.t = tt;
-                        h.b1 = bb1;
-                        h.b2 = bb2;
-                        h.prim = gid;
-                        found = true;
-                        if (any) return true;
-                    }
-                }
-            }
-        }
-        pa = pb = -1;
     }
     return found;
 }
