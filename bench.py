@@ -543,13 +543,18 @@ def run_reference(args):
     t0 = time.perf_counter()
     o.render_residual(spp, 1, 0, R)
     dt = time.perf_counter() - t0
-    R = max(64, int(R * 10.0 / max(dt, 1e-3)))
     N = o.n_roots(spp)
+    R = min(N, max(64, int(R * 10.0 / max(dt, 1e-3))))
+
+    def start(j):
+        # successive steps take successive root ranges, wrapping inside [0, N)
+        return (j * R) % (N - R) if N > R else 0
+
     for w in range(args.warmup):
-        o.render_residual(spp, 100 + w, (w * R) % (N - R), (w * R) % (N - R) + R)
+        o.render_residual(spp, 100 + w, start(w), start(w) + R)
     times = []
     for k in range(args.steps):
-        a = ((args.warmup + k) * R) % (N - R)
+        a = start(args.warmup + k)
         t0 = time.perf_counter()
         o.render_residual(spp, 1, a, a + R)
         times.append(time.perf_counter() - t0)
