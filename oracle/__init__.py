@@ -67,6 +67,8 @@ def lib():
                                              C.c_int, P, P]
         L.oracle_render_primal.argtypes = [P, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                            C.c_uint32, P]
+        L.oracle_render_primal_domain.argtypes = [P, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
+                                                  C.c_uint32, C.c_int, P]
         L.oracle_dump.restype = C.c_int64
         L.oracle_dump.argtypes = [P, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                   C.c_uint32, C.c_int, P, C.c_int64]
@@ -287,10 +289,14 @@ class Oracle:
                                      _p(cnt))
         return (img, cnt) if counters else img
 
-    def render_primal(self, frame, spp, seed, root_begin=0, root_end=None):
+    def render_primal(self, frame, spp, seed, root_begin=0, root_end=None, domain=0):
+        """Path-traced image of `frame`; domain != 0 keeps only the paths with a
+        dynamic vertex where a technique of the mask (bit 0: (1), bit 1: (2),
+        bit 2: (3)) would sample it (Sec. 4.1)."""
         img = np.zeros(self.shape)
         r1 = self.n_roots(spp) if root_end is None else root_end
-        lib().oracle_render_primal(self.h, frame, spp, seed, root_begin, r1, _p(img))
+        lib().oracle_render_primal_domain(self.h, frame, spp, seed, root_begin, r1, domain,
+                                          _p(img))
         return img
 
     def dump(self, tech, frame, spp, seed, root_begin, root_end, tech_mask=MASK_ALL,

@@ -1056,7 +1056,21 @@ typedef struct {
     int residual;           /* 0: primal (plain path tracing, no MIS) */
     int64_t counters[8];
     double vscale;          /* 0: none; else every emitted value is multiplied by it */
+    int domain;             /* primal only: 0 all paths; else bit t-1 keeps the paths with a
+                               dynamic vertex where technique t (1, 2, 3) would sample it */
 } sink;
+
+/* whether the path has a dynamic vertex at a position of a technique in
+ * `domain` (Sec. 4.1: (1) next to the emitter, (2) next to the sensor,
+ * (3) in between) */
+static int in_domain(const vtx *x, int n, int domain) {
+    for (int i = 1; i <= n - 2; ++i) {
+        if (!x[i].dyn) continue;
+        const int t = (i == n - 2) ? 1 : (i == 1) ? 2 : 3;
+        if ((domain >> (t - 1)) & 1) return 1;
+    }
+    return 0;
+}
 
 static void emit(sink *k, uint32_t root, int tech, int g, int sa, int sb, int pa, vec3 va, int pb,
                  vec3 vb, int status, double Pg, double Py, double J) {
@@ -1092,6 +1106,7 @@ static void evaluate_path(sink *k, int g, const vtx *x, int n, uint32_t root, in
     if (is_zero3(fx)) return;
     if (!k->residual) {
         /* primal path tracing: a single technique, no MIS */
+        if (k->domain && !in_domain(x, n, k->domain)) return;
         techmask only7 = {0, 0, 0, 1, 0, 0, 0};
         double p = mis_denominator(s, g, x, n, only7);
         emit(k, root, tech, g, sa, sb, pa, scale(fx, 1.0 / (k->N * p)), -1, v3(0, 0, 0), 0, p, 0,
@@ -1911,16 +1926,24 @@ int oracle_render_residual(void *h, uint32_t spp, uint64_t seed, uint32_t r0, ui
     return 0;
 }
 
-/* primal image of frame g by path tracing with next-event estimation */
-int oracle_render_primal(void *h, int g, uint32_t spp, uint64_t seed, uint32_t r0, uint32_t r1,
-                         double *img) {
+/* primal image of frame g by path tracing with next-event estimation,
+ * restricted to the paths of `domain` (in_domain; 0 keeps every path) */
+int oracle_render_primal_domain(void *h, int g, uint32_t spp, uint64_t seed, uint32_t r0,
+                                uint32_t r1, int domain, double *img) {
     oscene *s = (oscene *)h;
     sink k;
     memset(&k, 0, sizeof k);
     k.s = s; k.img = img; k.N = (double)spp * s->W * s->H;
     k.residual = 0;
+    k.domain = domain;
     run_roots(&k, TECH_PT, g, r0, r1, seed);
     return 0;
+}
+
+/* primal image of frame g by path tracing with next-event estimation */
+int oracle_render_primal(void *h, int g, uint32_t spp, uint64_t seed, uint32_t r0, uint32_t r1,
+                         double *img) {
+    return oracle_render_primal_domain(h, g, spp, seed, r0, r1, 0, img);
 }
 
 /* per-sample records of technique `tech` in frame g for roots [r0, r1) */

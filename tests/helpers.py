@@ -125,7 +125,7 @@ def _job(args):
         sys.path.insert(0, ROOT)
     import oracle
     from paper_2406_16302_gb300 import scenes
-    kind, builder, bargs, seed, spp, mask, edit_kind, guide = args
+    kind, builder, bargs, seed, spp, mask, edit_kind, guide, domain = args
     if isinstance(edit_kind, tuple) and edit_kind[0] == "objects":
         # objects 1..k of a several-object scene moved by d (one dynamic set)
         _, k, d = edit_kind
@@ -141,7 +141,8 @@ def _job(args):
         gseed, gkw = guide
         o.set_guide(scenes.random_int_guide(gseed, scenes.guide_box(scene.dyn_vertices), **gkw))
     if kind == "corr":
-        return o.render_primal(2, spp, seed) - o.render_primal(1, spp, seed)
+        return (o.render_primal(2, spp, seed, domain=domain)
+                - o.render_primal(1, spp, seed, domain=domain))
     if kind == "p1":
         return o.render_primal(1, spp, seed)
     if kind == "p2":
@@ -153,10 +154,13 @@ def _job(args):
     return o.render_residual(spp, seed, tech_mask=mask)
 
 
-def run_many(kind, builder, bargs, seeds, spp, mask=15, edit_kind=None, procs=None, guide=None):
+def run_many(kind, builder, bargs, seeds, spp, mask=15, edit_kind=None, procs=None, guide=None,
+             domain=0):
     """Independent oracle renders, one per seed.  guide = (seed, kwargs) of
-    a seeded integer proposal network for technique (3)."""
-    jobs = [(kind, builder, bargs, s, spp, mask, edit_kind, guide) for s in seeds]
+    a seeded integer proposal network for technique (3); domain restricts the
+    correlated path-traced difference to the paths of some of techniques
+    (1)-(3)."""
+    jobs = [(kind, builder, bargs, s, spp, mask, edit_kind, guide, domain) for s in seeds]
     procs = procs or min(len(jobs), os.cpu_count() or 1)
     if procs <= 1:
         return np.array([_job(j) for j in jobs])
