@@ -250,6 +250,13 @@ typedef struct {
 rp_status rp_enable_stats(rp_scene *scene, int on);
 rp_status rp_get_stats(rp_scene *scene, rp_stats *out);
 
+/* Waits for the work most recently enqueued on a scene's stream and reports
+ * how it ended: RP_OK, or RP_ERR_CUDA with the CUDA error text in
+ * rp_last_error() when a kernel or copy of it failed (render calls return
+ * launch errors at once but device-side failures only here or at the next
+ * synchronising call).  RP_ERR_INVALID_ARG for a null scene. */
+rp_status rp_sync_status(rp_scene *scene);
+
 /* Per-kernel device times of the wavefront kernels: when enabled, every
  * launch on a scene is bracketed by CUDA events recorded on its stream.
  * rp_get_kernel_times synchronises the scene's last stream, writes up to

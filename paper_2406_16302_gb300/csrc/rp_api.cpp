@@ -917,6 +917,13 @@ extern "C" rp_status rp_enable_stats(rp_scene *scene, int on) {
     return RP_OK;
 }
 
+extern "C" rp_status rp_sync_status(rp_scene *scene) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    RP_CUDA(cudaStreamSynchronize(scene->last_stream), "sync");
+    RP_CUDA(cudaGetLastError(), "device status");
+    return RP_OK;
+}
+
 extern "C" rp_status rp_get_stats(rp_scene *scene, rp_stats *out) {
     if (!scene || !out) return fail(RP_ERR_INVALID_ARG, "null argument");
     unsigned long long h[ST_COUNT];

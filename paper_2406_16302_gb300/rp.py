@@ -79,7 +79,8 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_multi", "r
            "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_f32_noalloc",
            "rp_render_residual_host",
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
-           "rp_enable_stats", "rp_get_stats", "rp_enable_timing", "rp_get_kernel_times",
+           "rp_enable_stats", "rp_get_stats", "rp_sync_status", "rp_enable_timing",
+           "rp_get_kernel_times",
            "rp_guide_create", "rp_guide_destroy", "rp_guide_set_weights", "rp_guide_get_weights",
            "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_encode", "rp_guide_loss_grad",
            "rp_guide_train_step", "rp_guide_status", "rp_scene_set_guide",
@@ -119,6 +120,7 @@ def lib():
         "rp_philox": (I, [U32, P, P, P, P]),
         "rp_enable_stats": (I, [P, I]),
         "rp_get_stats": (I, [P, P]),
+        "rp_sync_status": (I, [P]),
         "rp_enable_timing": (I, [P, I]),
         "rp_get_kernel_times": (I, [P, P, I, P]),
         "rp_guide_create": (I, [P, U32, U64, P]),
@@ -321,6 +323,11 @@ def rp_get_stats(scene: Scene) -> dict:
     s = rp_stats()
     _check(lib().rp_get_stats(scene.h, C.byref(s)))
     return {n: int(getattr(s, n)) for n, _ in rp_stats._fields_}
+
+
+def rp_sync_status(scene: Scene):
+    """Waits for the scene's queued work; raises on a device-side failure."""
+    _check(lib().rp_sync_status(scene.h))
 
 
 def rp_enable_timing(scene: Scene, on=True):

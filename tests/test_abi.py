@@ -52,3 +52,11 @@ def test_no_cpu_fallback(lib):
 def test_record_layout_matches_header():
     from paper_2406_16302_gb300 import rp
     assert rp.RECORD_DTYPE.itemsize == 68
+
+
+def test_null_arguments_are_refused_synchronously(lib):
+    """Argument errors come back at once, without touching a device."""
+    from paper_2406_16302_gb300 import rp
+    assert lib.rp_sync_status(None) == 1            # RP_ERR_INVALID_ARG
+    assert b"null" in lib.rp_last_error()
+    assert lib.rp_get_stats(None, None) == 1

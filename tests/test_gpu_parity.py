@@ -293,6 +293,7 @@ def test_identity_edit_is_exactly_zero_on_gpu(rp):
     ed = rp.Edit(sc, S.identity_edit(edit))
     img = rp.render_residual(sc, ed, 4, 9).cpu().numpy()
     assert np.all(img == 0.0)
+    rp.rp_sync_status(sc)                  # the render's kernels ended without a fault
 
 
 def test_f32_and_host_entry_points_agree(rp):
