@@ -205,7 +205,10 @@ rp_status rp_render_primal(rp_scene *scene, const rp_edit_handle *edit, int fram
  * (1, 2, 3 or 7 = path tracing) in one frame, for parity testing.  Each
  * base path with non-zero contribution yields one record; d_count receives
  * the number of records produced (may exceed capacity; only the first
- * `capacity` are written).  Asynchronous. */
+ * `capacity` are written).  This is the deterministic mode: each record's
+ * values are bitwise reproducible for (scene, edit, spp, seed) and carry no
+ * atomic summation; only the order of the records varies (sort by root,
+ * technique, frame and strategy).  Asynchronous. */
 typedef struct {
     uint32_t root;
     int32_t tech, frame;
