@@ -326,6 +326,8 @@ def test_root_ranges_partition_the_image(rp):
                 rec = rp.dump_samples(sc, ed, tech, frame, 4, 3, a, b)
                 parts += rec["va"].sum() + rec["vb"].sum()
     assert abs(parts - full.sum()) <= 1e-4 * np.abs(full).sum()
+    for tech in (1, 2, 3, 7):                      # an empty root range yields nothing
+        assert len(rp.dump_samples(sc, ed, tech, 1, 4, 3, 500, 500)) == 0
 
 
 def test_invalid_arguments_are_rejected(rp):
