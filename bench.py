@@ -37,8 +37,12 @@ sys.path.insert(0, ROOT)
 # determinant, 6 mul + 2 FMA for the distance, 1 reciprocal, 3 mul).
 FLOP_PER_NODE = 2 * (6 * 2 + 12 + 2)
 FLOP_PER_TRI = 9 + 6 * 2 + 9 + 2 + 6 + 2 * 2 + 1 + 3
-# GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA per clock
+# GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA per clock (nominal)
 SMS, FP32_LANES = 152, 128
+# measured on a GB300 by `python -m paper_2406_16302_gb300.peaks`
+# (profiles/device_peaks_gb300.md): reads from a 48 MB L2-resident buffer,
+# eight independent FMA chains per thread, FP64 atomicAdd on a 256x256x3 image
+DEVICE_PEAKS = {"l2_read_gbs": 17476.3, "fp32_fma_tflops": 69.82, "fp64_atomic_gops": 190.8}
 # algorithmic bytes of the traversal kernels, no cache credit: a node visit
 # reads one 64-byte two-child node, a triangle test one 48-byte triangle; a
 # closest-hit ray reads its 32-byte queue entry and writes a 28-byte hit, a
@@ -725,8 +729,14 @@ def main():
                                     "bytes_per_ray": BYTES_PER_RAY[dom]},
                 "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": peak_tflops,
                          "frac": achieved_tf / peak_tflops,
+                         "measured_peak_tflops": DEVICE_PEAKS["fp32_fma_tflops"],
+                         "frac_of_measured": achieved_tf / DEVICE_PEAKS["fp32_fma_tflops"],
                          "basis": f"152 SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz; "
                                   f"{FLOP_PER_NODE} flop per node, {FLOP_PER_TRI} per triangle"},
+                # the same algorithmic bytes against the measured L2 read
+                # bandwidth: the BVH of this scene is L2-resident
+                "l2": {"achieved": achieved, "peak": DEVICE_PEAKS["l2_read_gbs"], "unit": "GB/s",
+                       "frac": achieved / DEVICE_PEAKS["l2_read_gbs"]},
                 "share_of_step": ms_tot / max(sum(v[1] for v in kern.values()), 1e-9)}
     if rank != 0:
         if dist:
