@@ -232,6 +232,23 @@ rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edit, int fram
                            const float *d_origins, const float *d_dirs, float *d_t,
                            int32_t *d_prim, float *d_b1, float *d_b2, void *stream);
 
+/* The BVH that rp_scene_create builds for a mesh, built on the host only
+ * (no device needed), for inspection and tests.  verts: [n_verts][3] float;
+ * tris: [n_tris][3] vertex indices.  Writes *n_nodes (inner nodes) and
+ * *depth (inner levels); if nodes_out is not NULL it receives n_nodes x 16
+ * floats in the 64-byte node layout (four float4: child 0 x/y bounds,
+ * child 1 x/y bounds, both z bounds, then child0, child1, count0, count1 as
+ * int bits; a child >= 0 is an inner node, < 0 a leaf whose first triangle
+ * in leaf order is ~child), node_cap >= n_nodes; if tris_out is not NULL it
+ * receives n_tris x 12 floats (v0, v1, v2 as float4, v0.w = the triangle's
+ * index as int bits) in leaf order.  The binned-SAH build stands in for the
+ * ray-tracing library of the paper's implementation (Sec. 6).  Synchronous;
+ * RP_ERR_INVALID_ARG for null arguments, no triangles, an index out of
+ * range or a short node buffer. */
+rp_status rp_bvh_build_host(const float *verts, uint32_t n_verts, const uint32_t *tris,
+                            uint32_t n_tris, float *nodes_out, uint32_t node_cap,
+                            float *tris_out, uint32_t *n_nodes, int *depth);
+
 /* Philox4x32-10 on the device for n (counter[4], key[2]) pairs, for
  * known-answer tests.  Asynchronous. */
 rp_status rp_philox(uint32_t n, const uint32_t *d_counters, const uint32_t *d_keys,

@@ -903,6 +903,25 @@ extern "C" rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edi
     return RP_OK;
 }
 
+extern "C" rp_status rp_bvh_build_host(const float *verts, uint32_t n_verts, const uint32_t *tris,
+                                       uint32_t n_tris, float *nodes_out, uint32_t node_cap,
+                                       float *tris_out, uint32_t *n_nodes, int *depth) {
+    if (!verts || !tris || !n_nodes || !depth || n_tris == 0)
+        return fail(RP_ERR_INVALID_ARG, "null argument or no triangles");
+    if (n_tris > (1u << 30)) return fail(RP_ERR_INVALID_ARG, "too many triangles");
+    for (uint64_t i = 0; i < 3ull * n_tris; ++i)
+        if (tris[i] >= n_verts) return fail(RP_ERR_INVALID_ARG, "vertex index out of range");
+    BuiltBVH b = build_bvh(verts, tris, (int)n_tris, 0);
+    *n_nodes = (uint32_t)(b.nodes.size() / 4);
+    *depth = b.depth;
+    if (nodes_out) {
+        if (node_cap < *n_nodes) return fail(RP_ERR_INVALID_ARG, "node buffer too small");
+        std::memcpy(nodes_out, b.nodes.data(), b.nodes.size() * sizeof(float4));
+    }
+    if (tris_out) std::memcpy(tris_out, b.tris.data(), b.tris.size() * sizeof(float4));
+    return RP_OK;
+}
+
 extern "C" rp_status rp_philox(uint32_t n, const uint32_t *d_counters, const uint32_t *d_keys,
                                uint32_t *d_out, void *stream) {
     if (rp_status s = need_device()) return s;

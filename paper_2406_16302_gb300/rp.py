@@ -79,6 +79,7 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_multi", "r
            "rp_render_residual", "rp_render_residual_f32", "rp_render_residual_f32_noalloc",
            "rp_render_residual_host",
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
+           "rp_bvh_build_host",
            "rp_enable_stats", "rp_get_stats", "rp_sync_status", "rp_enable_timing",
            "rp_get_kernel_times",
            "rp_guide_create", "rp_guide_destroy", "rp_guide_set_weights", "rp_guide_get_weights",
@@ -121,6 +122,7 @@ def lib():
         "rp_enable_stats": (I, [P, I]),
         "rp_get_stats": (I, [P, P]),
         "rp_sync_status": (I, [P]),
+        "rp_bvh_build_host": (I, [P, C.c_uint32, P, C.c_uint32, P, C.c_uint32, P, P, P]),
         "rp_enable_timing": (I, [P, I]),
         "rp_get_kernel_times": (I, [P, P, I, P]),
         "rp_guide_create": (I, [P, U32, U64, P]),
@@ -323,6 +325,22 @@ def rp_get_stats(scene: Scene) -> dict:
     s = rp_stats()
     _check(lib().rp_get_stats(scene.h, C.byref(s)))
     return {n: int(getattr(s, n)) for n, _ in rp_stats._fields_}
+
+
+def rp_bvh_build_host(vertices, triangles) -> dict:
+    """The scene BVH of a mesh, built on the host: {"nodes": (n, 16) float32,
+    "tris": (t, 12) float32 in leaf order, "depth": int}."""
+    v = np.ascontiguousarray(vertices, dtype=np.float32)
+    t = np.ascontiguousarray(triangles, dtype=np.uint32)
+    n_nodes, depth = C.c_uint32(), C.c_int()
+    L = lib()
+    _check(L.rp_bvh_build_host(v.ctypes.data, len(v), t.ctypes.data, len(t), None, 0, None,
+                               C.byref(n_nodes), C.byref(depth)))
+    nodes = np.zeros((n_nodes.value, 16), dtype=np.float32)
+    tris = np.zeros((len(t), 12), dtype=np.float32)
+    _check(L.rp_bvh_build_host(v.ctypes.data, len(v), t.ctypes.data, len(t), nodes.ctypes.data,
+                               n_nodes.value, tris.ctypes.data, C.byref(n_nodes), C.byref(depth)))
+    return {"nodes": nodes, "tris": tris, "depth": depth.value}
 
 
 def rp_sync_status(scene: Scene):
