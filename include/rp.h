@@ -114,6 +114,9 @@ typedef struct rp_edit_s rp_edit_handle;
  * emitter, no dynamic triangle, max_depth outside [2, 12], emissive dynamic
  * material), RP_ERR_OOM, RP_ERR_CUDA. */
 rp_status rp_scene_create(const rp_scene_desc *desc, rp_scene **out);
+/* Frees a scene and its device memory (NULL: no-op).  Destroy the edits,
+ * guides attached to it and batches made from it first; the frees wait for
+ * the device, so queued work that uses the scene completes first. */
 void rp_scene_destroy(rp_scene *scene);
 
 /* An edit: the dynamic object's object-to-world transform (row-major 3x4)
@@ -131,6 +134,9 @@ typedef struct {
     uint32_t object;
 } rp_edit_desc;
 
+/* Errors: RP_ERR_INVALID_ARG (null pointers, object out of range, bad
+ * material), RP_ERR_UNSUPPORTED (non-rigid transform, emissive material),
+ * RP_ERR_OOM. */
 rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **out);
 
 /* An edit of n objects at once (1 <= n <= 8; Sec. 6 measures scenes with
@@ -148,6 +154,8 @@ rp_status rp_edit(rp_scene *scene, const rp_edit_desc *desc, rp_edit_handle **ou
  * learned proposal renders edits of one object only (RP_ERR_UNSUPPORTED). */
 rp_status rp_edit_multi(rp_scene *scene, const rp_edit_desc *descs, uint32_t n,
                         rp_edit_handle **out);
+/* Frees an edit and its device tables (NULL: no-op); no render or batch that
+ * uses it may still be queued. */
 void rp_edit_destroy(rp_edit_handle *edit);
 
 /* Residual image I2 - I1 (Eq. shiftmapped restricted to dynamic paths,
@@ -331,6 +339,7 @@ typedef struct rp_guide_s rp_guide;
  * technique (3) samples as without a guide and only collects samples.
  * Synchronous.  Errors: RP_ERR_INVALID_ARG, RP_ERR_OOM, RP_ERR_CUDA. */
 rp_status rp_guide_create(const float *box, uint32_t batch, uint64_t seed, rp_guide **out);
+/* Frees a guide (NULL: no-op); detach it from its scene first. */
 void rp_guide_destroy(rp_guide *guide);
 
 /* Float network weights (host arrays of 20480 floats); setting resets Adam. */
@@ -415,6 +424,7 @@ typedef struct rp_batch_s rp_batch;
  * used.  Synchronous.  Errors: RP_ERR_INVALID_ARG, RP_ERR_OOM, RP_ERR_CUDA. */
 rp_status rp_batch_create(rp_scene *scene, const rp_batch_item *items, uint32_t n,
                           const rp_batch_config *config, rp_batch **out);
+/* Frees a batch, its CUDA graph and its wave buffers (NULL: no-op). */
 void rp_batch_destroy(rp_batch *batch);
 /* One graph launch on `stream`: every item's residual added to its image. */
 rp_status rp_batch_launch(rp_batch *batch, void *stream);
