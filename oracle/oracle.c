@@ -55,7 +55,9 @@
  * the closed-form polygon irradiance; residual by exact zero for identity
  * edits, the closed-form moving-quad residual, agreement with the difference
  * of independent primal renders, mapping bijectivity and finite-difference
- * Jacobians.  Learned proposal: vMF density and sampler by quadrature and the
+ * Jacobians; the balance heuristic's terms by brute-force counts of dynamic
+ * vertices and ghost crossings; each of techniques (1)-(3) alone by path
+ * tracing restricted to its domain.  Learned proposal: vMF density and sampler by quadrature and the
  * closed-form cosine CDF, encoding by known angles, integer network by
  * hand-built networks, float gradient by finite differences, guided
  * estimator by agreement with correlated path tracing.
