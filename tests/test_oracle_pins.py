@@ -312,3 +312,23 @@ def test_rotation_edit_mapping(oracle_mod):
             if r["fd_checked"]:
                 assert r["max_fd_err"] < 1e-5, r
     assert total > 200
+
+
+@pytest.mark.parametrize("alpha", [0.05, 0.3, 0.8])
+def test_bsdf_textbook_values(oracle_mod, alpha):
+    """Closed forms of the two BSDFs (Lambert; Walter et al. 2007 GGX with
+    Smith masking and Schlick Fresnel): at normal incidence and normal exit
+    D = 1 / (pi alpha^2), G = 1, F = F0, so f = F0 / (4 pi alpha^2); Lambert
+    is rho / pi everywhere above the surface."""
+    n = np.array([0.0, 0.0, 1.0])
+    f0 = np.array([0.04, 0.5, 0.9])
+    rho, _ = oracle_mod.bsdf(S.material(S.GGX, alpha=alpha, f0=tuple(f0)), n, n, n)
+    np.testing.assert_allclose(rho, f0 / (4 * np.pi * alpha ** 2), rtol=1e-6)
+    lam = S.material(S.LAMBERT, (0.7, 0.5, 0.3))
+    wi = np.array([np.sin(0.4), 0.0, np.cos(0.4)])
+    wo = np.array([0.0, np.sin(1.1), np.cos(1.1)])
+    rho, _ = oracle_mod.bsdf(lam, n, wi, wo)
+    np.testing.assert_allclose(rho, np.array([0.7, 0.5, 0.3]) / np.pi, rtol=1e-6)
+    # below the surface nothing is reflected
+    rho, _ = oracle_mod.bsdf(lam, n, wi, -wo)
+    assert np.all(rho == 0)
