@@ -1,9 +1,13 @@
 """Benchmark: residual samples/s of the residual path integral estimator on GB300.
 
-Workload (default): the material-edit box scene at 256x256, 64 spp, max depth
-8 -- a Cornell-style box with a static sphere and a 20480-triangle seeded
-blob that changes from Lambert (albedo 0.8) to GGX (alpha 0.3, F0 0.04);
-techniques (1), (2), (3) and path tracing with rejection, both frames.
+Workload (default, `terrain_motion_1024`): the scale configuration -- a
+seeded fBm terrain of about 1M triangles with 200 instanced Lambert/GGX
+primitives, a 50k-triangle object rotated by 10 degrees and translated by 5 %
+of the scene extent between the frames; 1024x1024, 256 spp, max depth 8;
+techniques (1), (2), (3) and path tracing with rejection, both frames, every
+base path mapped into the other frame (object transform, camera replay,
+reconnection, random replay) and weighted by the two-way balance heuristic.
+`--workload box_blob_material_256` runs the material edit (256x256, 64 spp).
 
 One step = one residual render of the whole image (every root of every
 technique in both frames), i.e. one rp_render_residual call.  A residual sample = one root
@@ -12,7 +16,9 @@ mapped paths, MIS denominators and splats; a step processes
 spp * W * H * 4 * 2 of them.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
-bounded sample of the same workload instead.
+bounded sample of the same workload instead.  `--workload device_peaks`
+measures the L2 read bandwidth and FP32 FMA rate that the traversal
+roofline uses beside the HBM copy bandwidth.
 """
 from __future__ import annotations
 
@@ -39,23 +45,24 @@ FLOP_PER_NODE = 2 * (6 * 2 + 12 + 2)
 FLOP_PER_TRI = 9 + 6 * 2 + 9 + 2 + 6 + 2 * 2 + 1 + 3
 # GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA per clock (nominal)
 SMS, FP32_LANES = 152, 128
-# measured on a GB300 by `python -m paper_2406_16302_gb300.peaks`
-# (profiles/device_peaks_gb300.md): reads from a 48 MB L2-resident buffer,
-# eight independent FMA chains per thread, FP64 atomicAdd on a 256x256x3 image
-DEVICE_PEAKS = {"l2_read_gbs": 17476.3, "fp32_fma_tflops": 69.82, "fp64_atomic_gops": 190.8}
+# The L2 read bandwidth and FP32 FMA rate are measured in every run by the
+# probe below (device_peaks()); the HBM copy bandwidth comes from
+# MEASURED_PEAKS.json.
 # algorithmic bytes of the traversal kernels, no cache credit: a node visit
 # reads one 64-byte two-child node, a triangle test one 48-byte triangle; a
 # closest-hit ray reads its 32-byte queue entry and writes a 28-byte hit, a
 # shadow ray reads a 40-byte entry
 BYTES_PER_NODE, BYTES_PER_TRI = 64, 48
 BYTES_PER_RAY = {"k_trace_closest": 32 + 28, "k_trace_shadow": 40}
-# DRAM traffic of k_trace_closest from an ncu capture of every closest-hit
-# launch of one box_blob_material_256 render at 32 spp
-# (profiles/k_trace_closest_box_blob_material_256.md): dram read + write bytes
-# per traced ray, valid while the kernel's sources hash to KERNEL_SOURCES_SHA
-TRAFFIC_CAPTURE = {"kernel": "k_trace_closest", "workload": "box_blob_material_256",
-                   "dram_bytes_per_ray": (2126.010368e6 + 445.262080e6) / 57820270.0,
-                   "sources_sha": "ca6e970db6ab6a9a"}
+# DRAM traffic of the dominant traversal kernel per workload, from ncu
+# captures of every launch of that kernel in one render at reduced spp
+# (profiles/k_trace_closest_*.md): dram read + write bytes per traced ray,
+# valid while the kernel's sources hash to sources_sha
+TRAFFIC_CAPTURE = {
+    "box_blob_material_256": {"kernel": "k_trace_closest",
+                              "dram_bytes_per_ray": (2126.010368e6 + 445.262080e6) / 57820270.0,
+                              "sources_sha": "ca6e970db6ab6a9a"},
+}
 KERNEL_SOURCES = ["rp_device.cuh", "k_wave.cu", "rp_internal.h", "rp_wave.h"]
 
 
@@ -67,6 +74,119 @@ def kernel_sources_sha():
             h.update(fh.read())
     return h.hexdigest()[:16]
 
+
+
+# A standalone probe of the device peaks that the traversal roofline needs
+# besides the HBM copy bandwidth: the read bandwidth of an L2-resident buffer
+# (48 MB read 20 times per launch with __ldcg, which caches in L2 and not in
+# L1) and the FP32 FMA rate (eight independent FMA chains per thread).  It
+# prints one JSON object; compiled on first use into the package's build
+# folder.
+_PEAKS_CU = r"""
+#include <cuda_runtime.h>
+#include <cstdio>
+#include <cstdlib>
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { \
+    std::fprintf(stderr, "%s: %s\n", #x, cudaGetErrorString(e_)); std::exit(1); } } while (0)
+__global__ void l2_read(const float4 *__restrict__ buf, size_t n4, int reps, float *out) {
+    float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += step) {
+            const float4 v = __ldcg(buf + i);
+            a += v.x; b += v.y; c += v.z; d += v.w;
+        }
+    if (a + b + c + d == -1.2345f) out[0] = a;
+}
+__global__ void fma_rate(float *out, int iters, float m, float k) {
+    float x[8];
+    for (int j = 0; j < 8; ++j) x[j] = threadIdx.x * 1e-3f + j;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fmaf(x[j], m, k);
+    float s = 0.f;
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == -1.2345f) out[0] = s;
+}
+__global__ void atomics(double *img, unsigned n_img, unsigned long long n_add) {
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_add;
+         i += step)
+        atomicAdd(img + (unsigned)((i * 2654435761ull) % n_img), 1e-9);
+}
+template <class F> static float best_ms(F f, int runs) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a)); CK(cudaEventCreate(&b));
+    f(); CK(cudaDeviceSynchronize());
+    float best = 1e30f;
+    for (int r = 0; r < runs; ++r) {
+        CK(cudaEventRecord(a)); f(); CK(cudaEventRecord(b)); CK(cudaEventSynchronize(b));
+        float ms = 0.f; CK(cudaEventElapsedTime(&ms, a, b)); if (ms < best) best = ms;
+    }
+    return best;
+}
+int main() {
+    int dev = 0, sms = 0, l2 = 0, clk = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    CK(cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev));
+    float *out = nullptr; CK(cudaMalloc(&out, sizeof(float)));
+    const size_t bytes = 48ull << 20, n4 = bytes / sizeof(float4);
+    const int reps = 20;
+    float4 *buf = nullptr; CK(cudaMalloc(&buf, bytes)); CK(cudaMemset(buf, 0, bytes));
+    const float l2_ms = best_ms([&] { l2_read<<<sms * 8, 256>>>(buf, n4, reps, out); }, 5);
+    CK(cudaGetLastError());
+    const int iters = 1 << 16, blocks = sms * 8, threads = 256;
+    const float f_ms = best_ms([&] { fma_rate<<<blocks, threads>>>(out, iters, 0.9999999f, 1e-7f); }, 5);
+    CK(cudaGetLastError());
+    const unsigned n_img = 256u * 256u * 3u;
+    const unsigned long long n_add = 1ull << 26;
+    double *img = nullptr; CK(cudaMalloc(&img, sizeof(double) * n_img));
+    CK(cudaMemset(img, 0, sizeof(double) * n_img));
+    const float a_ms = best_ms([&] { atomics<<<sms * 8, 256>>>(img, n_img, n_add); }, 3);
+    CK(cudaGetLastError());
+    std::printf("{\"sms\": %d, \"l2_bytes\": %d, \"clock_mhz_attr\": %.0f, "
+                "\"l2_read_gbs\": %.1f, \"l2_read_buffer_mb\": %zu, \"fp32_fma_tflops\": %.2f, "
+                "\"fp64_atomic_gops\": %.2f, \"fp64_atomic_image\": \"256x256x3 doubles\"}\n",
+                sms, l2, clk / 1e3, (double)bytes * reps / (l2_ms * 1e-3) / 1e9, bytes >> 20,
+                16.0 * iters * (double)blocks * threads / (f_ms * 1e-3) / 1e12,
+                (double)n_add / (a_ms * 1e-3) / 1e9);
+    CK(cudaFree(buf)); CK(cudaFree(img)); CK(cudaFree(out));
+    return 0;
+}
+"""
+
+_PEAKS = None
+
+
+def build_peak_probe():
+    """Compile the probe (once per source version); returns the executable."""
+    import hashlib
+    from paper_2406_16302_gb300.build import ARCH, OUT_DIR, nvcc
+    tag = hashlib.sha256(_PEAKS_CU.encode()).hexdigest()[:12]
+    exe = os.path.join(OUT_DIR, f"bench_peaks_{tag}")
+    if not os.path.exists(exe):
+        os.makedirs(OUT_DIR, exist_ok=True)
+        src = exe + ".cu"
+        with open(src, "w") as f:
+            f.write(_PEAKS_CU)
+        r = subprocess.run([nvcc(), "-O3", "-std=c++17", src, "-o", exe] + ARCH,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"compiling the peak probe failed:\n{r.stderr}")
+    return exe
+
+
+def device_peaks():
+    """L2 read bandwidth and FP32 FMA rate of this GPU, measured once per
+    process by the probe above (a few hundred milliseconds)."""
+    global _PEAKS
+    if _PEAKS is None:
+        out = subprocess.run([build_peak_probe()], capture_output=True, text=True,
+                             check=True).stdout
+        _PEAKS = json.loads(out.strip().splitlines()[-1])
+    return _PEAKS
 
 
 def workload(name):
@@ -82,7 +202,7 @@ def workload(name):
         return scene, edit, 64
     if name == "terrain_motion_1024":
         scene, edit = scenes.cfg3_terrain()
-        return scene, edit, 16
+        return scene, edit, 256
     if name == "batch_32_edits":
         # one item as a single-object problem (the oracle arm)
         scene, frames = batch_workload()
@@ -400,6 +520,29 @@ def equal_time_mse(rp, sc, ed, scene, spp, K=4, ref_renders=16, guide_iters=30, 
     return out
 
 
+MSE_SPP = 16             # spp of each render in the equal-time MSE comparison
+
+
+def e2e_calls(steps):
+    """Calls timed by the end-to-end leg: half the timed steps, 3 to 10."""
+    return max(3, min(10, steps // 2))
+
+
+def bvh_footprint(scene):
+    """Bytes of scene data the traversal kernels read: BVH nodes and leaf
+    triangles of the static scene and the dynamic mesh (from the library's
+    own host BVH builder) and the 48-byte triangles by id that the closest
+    hit's refinement reads."""
+    from paper_2406_16302_gb300 import rp
+    total = 0
+    for v, t in ((scene.static_vertices, scene.static_triangles),
+                 (scene.dyn_vertices, scene.dyn_triangles)):
+        if len(t):
+            b = rp.rp_bvh_build_host(v, np.asarray(t, np.uint32))
+            total += b["nodes"].nbytes + b["tris"].nbytes + 48 * len(t)
+    return int(total)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -493,6 +636,56 @@ def cpu_baseline(scene, edit, spp, target_s=15.0):
             "roots": R, "n_roots": o.n_roots(spp)}
 
 
+def compare_records(gpu, ora, rel=1e-4):
+    """Per-sample agreement of two record sets keyed by (root, technique,
+    frame, sa, sb): both splats on the same pixels and each value within
+    rel of the sample's magnitude.  Returns (matching, total, max relative
+    error over samples present on both sides)."""
+    def key(r):
+        return (int(r["root"]), int(r["tech"]), int(r["frame"]), int(r["sa"]), int(r["sb"]))
+    go = {key(r): r for r in gpu}
+    oo = {key(r): r for r in ora}
+    good, worst = 0, 0.0
+    for k in set(go) | set(oo):
+        g, o = go.get(k), oo.get(k)
+        if g is None or o is None:
+            continue
+        scale = max(float(np.abs(o["va"]).max()), float(np.abs(o["vb"]).max()), 1e-300)
+        err = max(float(np.abs(g["va"] - o["va"]).max()), float(np.abs(g["vb"] - o["vb"]).max()))
+        same_pix = g["pix_a"] == o["pix_a"] and g["pix_b"] == o["pix_b"]
+        if same_pix:
+            worst = max(worst, err / scale)
+        if same_pix and err <= rel * scale:
+            good += 1
+    return good, len(set(go) | set(oo)), worst
+
+
+def oracle_error(rp, sc, ed, scene, edit, spp, seed, ranges=8, width=32):
+    """Error of the timed workload's samples against the FP64 oracle: the
+    same seed's records of root ranges spread over the whole root range, every
+    technique and both frames, compared sample by sample (this is the
+    cpu_baseline leg's second use of the oracle)."""
+    import oracle
+    o = oracle.Oracle(scene, edit)
+    N = sc.n_roots(spp)
+    starts = np.linspace(0, N - width, ranges).astype(np.int64)
+    good = total = 0
+    worst = 0.0
+    for tech in (1, 2, 3, 7):
+        for frame in (1, 2):
+            g = np.concatenate([rp.dump_samples(sc, ed, tech, frame, spp, seed, int(a), int(a) + width)
+                                for a in starts])
+            r = np.concatenate([o.dump(tech, frame, spp, seed, int(a), int(a) + width)
+                                for a in starts])
+            ng, nt, w = compare_records(g, r)
+            good += ng
+            total += nt
+            worst = max(worst, w)
+    return {"rel_tol": 1e-4, "samples": total, "within_tol": good / max(total, 1),
+            "max_rel_err": worst, "roots": f"{ranges} ranges of {width} roots spread over [0, {N}) "
+                                            f"per technique and frame, seed {seed}"}
+
+
 def _oracle_worker(name, spp, a, R, seed, barrier, results):
     """One process of the multi-core oracle timing: roots [a, a+R) of every
     technique in both frames, started together with the others."""
@@ -584,7 +777,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="box_blob_material_256")
+    ap.add_argument("--workload", default="terrain_motion_1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE comparison")
@@ -599,6 +792,9 @@ def main():
         return run_batch(args)
     if args.workload in ("sweep_displacement", "sweep_objects"):
         return run_sweep(args)
+    if args.workload == "device_peaks":
+        print(json.dumps(device_peaks()), flush=True)
+        return
 
     import torch
     ws, rank, local = dist_env()
@@ -677,7 +873,7 @@ def main():
         host = np.zeros(sc.shape, dtype=np.float64)
         rp.rp_render_residual_host(sc, edit, spp, seed0, host)
         times = []
-        for k in range(max(1, min(args.steps, 3))):
+        for k in range(e2e_calls(args.steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rp.rp_render_residual_host(sc, edit, spp, seed0 + 200 + k, host)
@@ -688,8 +884,10 @@ def main():
                "h2d_bytes_per_step": 4 * 48, "d2h_bytes_per_step": int(host.nbytes),
                "ms_per_step": e_ms}
 
-    # roofline of the dominant traversal kernel (node box tests and triangle
-    # tests at the FP32 peak); every kernel's share is reported beside it
+    # roofline of the dominant traversal kernel: its algorithmic bytes (node
+    # visits, triangle tests, queue entries) per launch over its CUDA-event
+    # time, against the L2 read bandwidth when the BVH fits in L2 and the
+    # HBM copy bandwidth otherwise; FP32 work against the FMA rate beside it
     per_kernel = {k: {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
                       "share": ms / max(sum(v[1] for v in kern.values()), 1e-9)}
                   for k, (n, ms) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
@@ -704,52 +902,61 @@ def main():
                     + rays * BYTES_PER_RAY[dom]) / launches_one_step
     flops_launch = (nodes * FLOP_PER_NODE + tris * FLOP_PER_TRI) / launches_one_step
     peaks = measured_peaks()
+    probe = device_peaks()
     clock = clk.summary()
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES * 2 * peak_mhz * 1e6 / 1e12
+    peak_tflops = probe["sms"] * FP32_LANES * 2 * peak_mhz * 1e6 / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_launch / (launch_ms / 1e3) / 1e9
+    footprint = bvh_footprint(scene)
+    l2_resident = footprint <= probe["l2_bytes"]
     traffic = None
-    if (dom == TRAFFIC_CAPTURE["kernel"] and args.workload == TRAFFIC_CAPTURE["workload"]
-            and kernel_sources_sha() == TRAFFIC_CAPTURE["sources_sha"]):
-        # captured at 32 spp, scaled to this launch by its rays (queue traffic
-        # grows with the rays; the BVH stays in L2)
-        traffic = TRAFFIC_CAPTURE["dram_bytes_per_ray"] * rays / launches_one_step
+    cap = TRAFFIC_CAPTURE.get(args.workload)
+    if cap and dom == cap["kernel"] and kernel_sources_sha() == cap["sources_sha"]:
+        # DRAM bytes per traced ray of an ncu capture of the same kernel,
+        # scaled to this launch by its rays
+        traffic = cap["dram_bytes_per_ray"] * rays / launches_one_step
     achieved_tf = flops_launch / (launch_ms / 1e3) / 1e12
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic,
-                "kernel": dom, "launch_ms": launch_ms,
-                "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (measured copy bandwidth)"
-                              if "hbm_gbs" in peaks else "fallback 6800 GB/s",
+    hbm_basis = ("hbm_gbs of MEASURED_PEAKS.json (measured copy bandwidth)"
+                 if "hbm_gbs" in peaks else "fallback 6800 GB/s (MEASURED_PEAKS.json absent)")
+    l2_basis = "L2 read bandwidth measured in this run (48 MB resident buffer, __ldcg)"
+    roofline = {"bound": "l2" if l2_resident else "hbm", "achieved": achieved,
+                "peak": probe["l2_read_gbs"] if l2_resident else hbm, "unit": "GB/s",
+                "frac": achieved / (probe["l2_read_gbs"] if l2_resident else hbm),
+                "traffic": traffic, "kernel": dom, "launch_ms": launch_ms,
+                "peak_basis": l2_basis if l2_resident else hbm_basis,
+                "bvh_footprint_bytes": footprint, "l2_bytes": probe["l2_bytes"],
                 "bytes_per_launch": bytes_launch,
                 "work_per_launch": {"node_visits": nodes / launches_one_step,
                                     "triangle_tests": tris / launches_one_step,
                                     "rays": rays / launches_one_step,
                                     "bytes_per_node": BYTES_PER_NODE, "bytes_per_tri": BYTES_PER_TRI,
                                     "bytes_per_ray": BYTES_PER_RAY[dom]},
+                "hbm": {"achieved": achieved, "peak": hbm, "frac": achieved / hbm,
+                        "peak_basis": hbm_basis},
+                "l2": {"achieved": achieved, "peak": probe["l2_read_gbs"], "unit": "GB/s",
+                       "frac": achieved / probe["l2_read_gbs"], "peak_basis": l2_basis},
                 "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": peak_tflops,
                          "frac": achieved_tf / peak_tflops,
-                         "measured_peak_tflops": DEVICE_PEAKS["fp32_fma_tflops"],
-                         "frac_of_measured": achieved_tf / DEVICE_PEAKS["fp32_fma_tflops"],
-                         "basis": f"152 SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz; "
+                         "measured_peak_tflops": probe["fp32_fma_tflops"],
+                         "frac_of_measured": achieved_tf / probe["fp32_fma_tflops"],
+                         "basis": f"{probe['sms']} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz; "
                                   f"{FLOP_PER_NODE} flop per node, {FLOP_PER_TRI} per triangle"},
-                # the same algorithmic bytes against the measured L2 read
-                # bandwidth: the BVH of this scene is L2-resident
-                "l2": {"achieved": achieved, "peak": DEVICE_PEAKS["l2_read_gbs"], "unit": "GB/s",
-                       "frac": achieved / DEVICE_PEAKS["l2_read_gbs"]},
                 "share_of_step": ms_tot / max(sum(v[1] for v in kern.values()), 1e-9)}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     cpu = None
+    err = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(scene, edit, spp)
         cpu["multi_core"] = cpu_baseline_multicore(args.workload, spp, cpu["roots"],
                                                    cpu["n_roots"])
+        err = oracle_error(rp, sc, ed, scene, edit, spp, seed0 + 100)
     et_mse = None
     if not args.no_mse and ws == 1:
-        et_mse = equal_time_mse(rp, sc, ed, scene, spp)
+        et_mse = equal_time_mse(rp, sc, ed, scene, min(spp, MSE_SPP))
     line = {
         "metric": "residual samples/s", "value": value, "unit": "residual samples/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": worst_ms,
@@ -767,7 +974,8 @@ def main():
                    # splatted base paths per pixel (the paper's spp convention, Sec. 6)
                    "spp_equivalent": work["paths"] / (scene.camera.width * scene.camera.height)},
         "root_samples_per_s": value,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "equal_time_mse": et_mse,
+        "roofline": roofline, "cpu_baseline": cpu, "oracle_error": err, "e2e": e2e,
+        "equal_time_mse": et_mse,
         "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clock,
     }
     print(json.dumps(line), flush=True)

@@ -60,10 +60,3 @@ def test_null_arguments_are_refused_synchronously(lib):
     assert lib.rp_sync_status(None) == 1            # RP_ERR_INVALID_ARG
     assert b"null" in lib.rp_last_error()
     assert lib.rp_get_stats(None, None) == 1
-
-
-def test_peak_probe_builds():
-    """The device-peak probe compiles for sm_103a (it runs only on a GPU)."""
-    from paper_2406_16302_gb300 import peaks
-    exe = peaks.build()
-    assert os.path.exists(exe) and os.access(exe, os.X_OK)

@@ -61,3 +61,35 @@ def test_multicore_oracle_timing_uses_disjoint_ranges():
     d = bench.cpu_baseline_multicore("box_sphere_motion_64", 16, 64, 1 << 16, cores=2)
     assert d["kind"] == "oracle" and d["cores"] == 2 and d["value"] > 0
     assert "1024 residual samples" in d["sample"]
+
+
+def test_peak_probe_builds():
+    """The bench's device-peak probe compiles for sm_103a (it runs only on a
+    GPU)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    exe = bench.build_peak_probe()
+    assert os.path.exists(exe) and os.access(exe, os.X_OK)
+
+
+def test_record_comparison_counts_mismatches():
+    """compare_records (the bench's oracle_error) matches samples by key and
+    flags a moved pixel, a value beyond the tolerance and a missing sample."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_2406_16302_gb300.rp import RECORD_DTYPE
+    a = np.zeros(5, dtype=RECORD_DTYPE)
+    a["root"] = np.arange(5)
+    a["tech"] = 1
+    a["frame"] = 2
+    a["pix_a"] = 7
+    a["pix_b"] = -1
+    a["va"] = 1.0
+    b = a.copy()
+    b["va"][0] += 0.5e-4            # within 1e-4 of the magnitude
+    b["va"][1] += 3e-4              # beyond it
+    b["pix_a"][2] = 8               # another pixel
+    good, total, worst = bench.compare_records(b[:4], a)
+    assert (good, total) == (2, 5)
+    assert abs(worst - 3e-4) < 1e-6
