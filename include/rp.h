@@ -178,10 +178,19 @@ rp_status rp_render_residual_f32(rp_scene *scene, const rp_edit_handle *edit, ui
  * memory (they manage every byte through their own pool, run under a hard
  * memory cap, or forbid allocation after start-up because cudaMalloc may
  * synchronise the device).  Instead of a cudaMalloc'd scratch image the call
- * uses a fixed FP64 array compiled into the library's device image, so every
- * GPU that loads librp holds RP_NOALLOC_MAX_PIXELS * 3 doubles (24 MiB) until
- * the process exits.  Same arguments, result and accumulation into d_out as
- * rp_render_residual_f32.
+ * uses a fixed FP64 array of RP_NOALLOC_MAX_PIXELS * 3 doubles (24 MiB)
+ * compiled into the library's device image.  A device holds it from the
+ * first call on that device (CUDA loads the library's device code lazily by
+ * default) or from library load when CUDA_MODULE_LOADING=EAGER, until the
+ * process exits.  Same arguments and accumulation into d_out as
+ * rp_render_residual_f32, with two differences:
+ *   - it runs the one-thread-per-root kernels, which have no ghost
+ *     techniques: a tech_mask with any RP_TECH_GHOSTS bit returns
+ *     RP_ERR_UNSUPPORTED;
+ *   - a learned proposal attached to the scene (rp_scene_set_guide) is not
+ *     used, so with a guide the image differs from rp_render_residual_f32's
+ *     (both are unbiased estimates of the same residual).
+ * Errors and sharing:
  *   - width * height above RP_NOALLOC_MAX_PIXELS: RP_ERR_INVALID_ARG.
  *   - The first call on a device looks up the array's device address
  *     (once per device, with that device current); make that first call
@@ -262,9 +271,11 @@ rp_status rp_bvh_build_host(const float *verts, uint32_t n_verts, const uint32_t
 rp_status rp_philox(uint32_t n, const uint32_t *d_counters, const uint32_t *d_keys,
                     uint32_t *d_out, void *stream);
 
-/* Work counters of the most recent render on a scene (synchronises the
- * scene's last stream): roots, base paths splatted, rays traced by kind and
- * BVH nodes / triangles visited, used for the traversal roofline. */
+/* Work counters of the most recent render or rp_trace_closest call on a
+ * scene (synchronises the scene's last stream): roots, base paths splatted,
+ * rays traced by kind and BVH nodes / triangles visited, used for the
+ * traversal roofline.  rp_trace_closest counts its rays, node visits and
+ * triangle tests as closest-hit work. */
 typedef struct {
     unsigned long long roots;
     unsigned long long paths;
@@ -299,6 +310,14 @@ typedef struct {
 
 rp_status rp_enable_timing(rp_scene *scene, int on);
 rp_status rp_get_kernel_times(rp_scene *scene, rp_kernel_time *out, int capacity, int *count);
+
+/* Timing of one kernel only: like rp_enable_timing(scene, 1), but only the
+ * launches of the wavefront kernel named `kernel` (as rp_get_kernel_times
+ * names it, e.g. "k_trace_closest") are bracketed by events, so that the
+ * other launches run without them; NULL times every kernel.  The name is
+ * copied (at most 31 characters, else RP_ERR_INVALID_ARG).  Turned off by
+ * rp_enable_timing(scene, 0). */
+rp_status rp_enable_timing_of(rp_scene *scene, const char *kernel);
 
 /* ------------------------------------------------------------------------
  * Learned proposal for technique (3) (not in the paper, which names better
@@ -387,6 +406,19 @@ rp_status rp_guide_train_step(rp_guide *guide, float lr, float *loss, void *stre
  * the device). */
 rp_status rp_guide_status(rp_guide *guide);
 
+/* Self-test of the timeout path of the tensor-core kernels (the paper has no
+ * counterpart).  Runs one 128-row tile of the inference kernel with its
+ * tensor-core completion signal withheld and its barrier wait bounded by
+ * limit_ns (0 < limit_ns <= 2e9): nothing arrives at the barrier, the wait
+ * runs out, the kernel records the timeout, releases its tensor memory and
+ * returns, leaving the context usable.  Synchronous (device-wide).
+ * Returns RP_ERR_TIMEOUT when the wait ran out, which is the expected
+ * result, and clears the guide's timeout flag afterwards; RP_OK would mean
+ * that the wait did not give up.  RP_ERR_TIMEOUT without running anything
+ * when an earlier guide kernel's wait had already timed out (see
+ * rp_guide_status).  Allocates two small scratch buffers. */
+rp_status rp_guide_wait_selftest(rp_guide *guide, uint64_t limit_ns);
+
 /* Attach a guide to a scene's technique (3) for the renders that follow
  * (NULL detaches).  The guide must outlive its attachment.  The
  * one-thread-per-root entry point (rp_render_residual_f32_noalloc) never
@@ -413,8 +445,18 @@ typedef struct {
 
 typedef struct {
     uint32_t wave_roots;         /* roots per wave (0: min(largest item, 2^22)) */
-    uint32_t streams;            /* concurrent branches, 1..8 (0: 1) */
-    uint32_t blocks_per_sm;      /* grid of the queue kernels per SM, 1..64 (0: 16) */
+    uint32_t streams;            /* graph mode: concurrent branches, 1..8 (0: 1);
+                                    persistent mode: waves per round, 1..128 (0: 8) */
+    uint32_t blocks_per_sm;      /* graph mode: grid of the queue kernels per SM, 1..64 (0: 16);
+                                    persistent mode: at most this many resident blocks per
+                                    SM (0: as many as fit) */
+    uint32_t persistent;         /* 0: a graph of per-wave kernel launches over `streams`
+                                    branches; 1: rounds of `streams` waves (jobs: one wave of
+                                    one item's technique and frame, each with its own wave
+                                    buffers), each round one cooperative launch of a
+                                    persistent kernel whose blocks pull (job, chunk) work
+                                    items of every stage from a device counter, with a
+                                    grid barrier between stages */
 } rp_batch_config;
 
 typedef struct rp_batch_s rp_batch;
@@ -430,6 +472,10 @@ void rp_batch_destroy(rp_batch *batch);
 rp_status rp_batch_launch(rp_batch *batch, void *stream);
 /* Stream-ordered upload of new per-item seeds (n values) for later launches. */
 rp_status rp_batch_set_seeds(rp_batch *batch, const uint64_t *seeds, void *stream);
+/* Synchronises the device and returns RP_ERR_TIMEOUT if a grid barrier of
+ * the persistent kernel gave up (after about 2 s of waiting; the launch then
+ * ended early and the images are incomplete), else RP_OK. */
+rp_status rp_batch_status(rp_batch *batch);
 /* The configuration in use and the number of graph nodes. */
 rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *graph_nodes);
 /* Autotuner: times candidate configurations on a proxy of the batch (each

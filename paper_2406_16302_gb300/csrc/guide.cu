@@ -22,6 +22,8 @@
 
 namespace rp {
 
+int device_sm_count();          // k_misc.cu
+
 namespace {
 
 constexpr uint64_t kWaitNs = 2000000000ull;     // tensor-core waits give up after 2 s
@@ -59,8 +61,12 @@ __device__ __forceinline__ void store8(unsigned char *tile, int row, int k, int 
     *reinterpret_cast<uint4 *>(tile + tc::kmaj_off(row, k, K)) = *reinterpret_cast<uint4 *>(p);
 }
 
+// withhold: the self-test of the timeout path (rp_guide_wait_selftest)
+// issues no MMA and no commit, so nothing arrives at the barrier and the
+// bounded wait runs out after limit_ns
 __global__ void __launch_bounds__(128) k_guide_infer(const GuideNet net, const int8_t *__restrict__ m_in,
-                                                     uint32_t n, float *__restrict__ out, int *err) {
+                                                     uint32_t n, float *__restrict__ out, int *err,
+                                                     uint64_t limit_ns, int withhold) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kI_MBAR);
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(128) k_guide_infer(const GuideNet net, const i
         __syncthreads();
         for (int l = 0; l < kGLayers; ++l) {
             const int K = guide_in(l), N = guide_out(l);
-            if (tid == 0) {
+            if (tid == 0 && !withhold) {
                 tc::fence_after_sync();
                 const uint32_t b_addr = tc::smem_u32(sm + kI_W + w_tile_off(l));
                 for (int ks = 0; ks < K / 16; ++ks)
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(128) k_guide_infer(const GuideNet net, const i
                 tc::commit(mbar);
             }
             __syncwarp();
-            const int got = tc::mbar_wait(mbar, phase, kWaitNs) ? 1 : 0;
+            const int got = tc::mbar_wait(mbar, phase, limit_ns) ? 1 : 0;
             phase ^= 1u;
             tc::fence_after_sync();
             ok = __syncthreads_and(got);
@@ -141,8 +147,9 @@ __global__ void __launch_bounds__(128) k_guide_infer(const GuideNet net, const i
         }
     }
     if (!ok) {
-        // let a late MMA finish before the tensor memory is released
-        tc::mbar_wait(mbar, phase ^ 1u, kWaitNs);
+        // let a late MMA finish before the tensor memory is released (none
+        // was issued when withheld)
+        if (!withhold) tc::mbar_wait(mbar, phase ^ 1u, limit_ns);
         if (tid == 0) atomicExch(err, 1);
     }
     tc::fence_before_sync();
@@ -485,17 +492,6 @@ __global__ void k_guide_adam(float *W, float *m, float *v, const float *grad, __
     }
 }
 
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
-    }
-    return n;
-}
-
 }  // namespace
 
 cudaError_t launch_guide_infer(const GuideNet &net, const int8_t *m_in, uint32_t n, float *out,
@@ -509,8 +505,17 @@ cudaError_t launch_guide_infer(const GuideNet &net, const int8_t *m_in, uint32_t
         attr = true;
     }
     const uint32_t tiles = (n + 127u) / 128u;
-    const uint32_t grid = tiles < (uint32_t)(3 * sm_count()) ? tiles : (uint32_t)(3 * sm_count());
-    k_guide_infer<<<grid, 128, kI_SMEM, s>>>(net, m_in, n, out, err);
+    const uint32_t grid = tiles < (uint32_t)(3 * device_sm_count()) ? tiles : (uint32_t)(3 * device_sm_count());
+    k_guide_infer<<<grid, 128, kI_SMEM, s>>>(net, m_in, n, out, err, kWaitNs, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guide_wait_selftest(const GuideNet &net, const int8_t *m_in, float *out, int *err,
+                                       uint64_t limit_ns, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_guide_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kI_SMEM);
+    if (e != cudaSuccess) return e;
+    k_guide_infer<<<1, 128, kI_SMEM, s>>>(net, m_in, 128u, out, err, limit_ns, 1);
     return cudaGetLastError();
 }
 
@@ -524,7 +529,7 @@ cudaError_t launch_guide_train(const GuideTrain &t, cudaStream_t s) {
         attr = true;
     }
     const uint32_t tiles = (t.n + 127u) / 128u;
-    const uint32_t grid = tiles < (uint32_t)sm_count() ? tiles : (uint32_t)sm_count();
+    const uint32_t grid = tiles < (uint32_t)device_sm_count() ? tiles : (uint32_t)device_sm_count();
     k_guide_train<<<grid, 128, kT_SMEM, s>>>(t);
     return cudaGetLastError();
 }

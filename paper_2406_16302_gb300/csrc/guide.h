@@ -56,6 +56,10 @@ struct GuideTrain {
 cudaError_t launch_guide_infer(const GuideNet &net, const int8_t *m_in, uint32_t n, float *out,
                                int *err, cudaStream_t s);
 cudaError_t launch_guide_train(const GuideTrain &t, cudaStream_t s);
+// one tile of the inference kernel with its MMA completion withheld and the
+// barrier wait bounded by limit_ns (the timeout path's self-test)
+cudaError_t launch_guide_wait_selftest(const GuideNet &net, const int8_t *m_in, float *out, int *err,
+                                       uint64_t limit_ns, cudaStream_t s);
 // training batch from the samples: features, directions, weights, and the
 // sum of the weights into *wsum
 cudaError_t launch_guide_features(const GuideSamples &smp, const float *box, uint32_t n,

@@ -27,32 +27,42 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ Launch
                                                   int32_t *prim, float *b1, float *b2) {
     __shared__ int s_stack[kStackDepth * kBlock];
     Ctx c(A, s_stack + threadIdx.x);
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Hit h;
-    float3 oo = f3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
-    float3 dd = f3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
-    if (scene_trace(c, A.frame, oo, dd, 0.0f, __int_as_float(0x7f800000), -1, -1, false, false, h)) {
-        t[i] = h.t;
-        prim[i] = h.prim;
-        b1[i] = h.b1;
-        b2[i] = h.b2;
-    } else {
-        t[i] = __int_as_float(0x7f800000);
-        prim[i] = -1;
-        b1[i] = 0.f;
-        b2[i] = 0.f;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {      // no early return: the counters below are summed over whole warps
+        Hit h;
+        const float3 oo = f3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+        const float3 dd = f3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+        ++c.cnt.rays_closest;
+        if (scene_trace(c, A.frame, oo, dd, 0.0f, __int_as_float(0x7f800000), -1, -1, false, false, h)) {
+            t[i] = h.t;
+            prim[i] = h.prim;
+            b1[i] = h.b1;
+            b2[i] = h.b2;
+        } else {
+            t[i] = __int_as_float(0x7f800000);
+            prim[i] = -1;
+            b1[i] = 0.f;
+            b2[i] = 0.f;
+        }
+    }
+    if (A.stats) {
+        add_stat(A.stats, ST_RAYS_CLOSEST, c.cnt.rays_closest);
+        add_stat(A.stats, ST_NODES, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS, c.cnt.tris);
+        add_stat(A.stats, ST_NODES_C, c.cnt.nodes);
+        add_stat(A.stats, ST_TRIS_C, c.cnt.tris);
     }
 }
 
 cudaError_t launch_trace(const DevScene &S, const DevEdit &E, int frame, uint32_t n, const float *o,
                          const float *d, float *t, int32_t *prim, float *b1, float *b2,
-                         cudaStream_t s) {
+                         unsigned long long *stats, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     LaunchArgs a{};
     a.S = S;
     a.E = E;
     a.frame = frame;
+    a.stats = stats;
     k_trace<<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(a, n, o, d, t, prim, b1, b2);
     return cudaGetLastError();
 }
@@ -82,10 +92,25 @@ __global__ void k_add_f64_to_f32(const double *src, float *dst, size_t n) {
         dst[i] += (float)src[i];
 }
 
+int device_sm_count() {
+    // per device, looked up once (attribute queries are not stream work, so
+    // this is safe inside a stream capture)
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < 64 && cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        n = 1;
+    if (dev < 64) cache[dev] = n;
+    return n;
+}
+
 cudaError_t launch_add_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     int grid = (int)((n + 255) / 256);
-    if (grid > 152 * 8) grid = 152 * 8;
+    const int cap = device_sm_count() * 8;       // 8 resident blocks of 256 per SM
+    if (grid > cap) grid = cap;
     k_add_f64_to_f32<<<grid, 256, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -703,6 +705,20 @@ static rp_status alloc_wavebuf(WaveBuf &W, std::vector<void *> &allocs, uint32_t
         A_(W.v_ex0, W.qv * 4ull) A_(W.v_ex1, W.qv * 4ull) A_(W.v_task, W.qv * 4ull)
         A_(W.m_pix, W.qt * 8ull) A_(W.m_val, W.qt * 36ull) A_(W.m_w, W.qt * 12ull)
         A_(W.m_vis, W.qt * 4ull) A_(W.pend, W.qt * 4ull)
+        // wavefront mapping: state per task, a pool of replayed vertices
+        // (tasks that find it full map in one thread), replay queues
+        W.yc = (uint32_t)std::min<uint64_t>((uint64_t)R * 12u, 0x7ffffffeull);
+        W.qr = (uint32_t)std::min<uint64_t>((uint64_t)R * 4u, W.qt);
+        A_(W.ms_info, W.qt * 4ull) A_(W.ms_J, W.qt * 4ull) A_(W.ms_base, W.qt * 4ull)
+        A_(W.fin, W.qt * 4ull)
+        A_(W.y_p, W.yc * 12ull) A_(W.y_n, W.yc * 12ull) A_(W.y_b, W.yc * 8ull)
+        A_(W.y_prim, W.yc * 4ull)
+        for (int b = 0; b < 2; ++b) {
+            A_(W.r_o[b], W.qr * 12ull) A_(W.r_d[b], W.qr * 12ull) A_(W.r_ex[b], W.qr * 4ull)
+            A_(W.r_task[b], W.qr * 4ull)
+        }
+        A_(W.rh_prim, W.qr * 4ull) A_(W.rh_b1, W.qr * 4ull) A_(W.rh_b2, W.qr * 4ull)
+        A_(W.rh_p, W.qr * 12ull)
     }
     A_(W.counts, kCountSlots * 4ull)
 #undef A_
@@ -897,8 +913,11 @@ extern "C" rp_status rp_trace_closest(rp_scene *scene, const rp_edit_handle *edi
     if (frame != 1 && frame != 2) return fail(RP_ERR_INVALID_ARG, "frame must be 1 or 2");
     if (n && (!d_origins || !d_dirs || !d_t || !d_prim || !d_b1 || !d_b2))
         return fail(RP_ERR_INVALID_ARG, "null ray buffer");
+    if (scene->stats_on)
+        RP_CUDA(cudaMemsetAsync(scene->d_stats, 0, sizeof(unsigned long long) * ST_COUNT,
+                                (cudaStream_t)stream), "memset");
     RP_CUDA(launch_trace(scene_for_edit(scene, edit->E), edit->E, frame, n, d_origins, d_dirs, d_t, d_prim, d_b1, d_b2,
-                         (cudaStream_t)stream),
+                         scene->stats_on ? scene->d_stats : nullptr, (cudaStream_t)stream),
             "trace launch");
     return RP_OK;
 }
@@ -966,6 +985,17 @@ extern "C" rp_status rp_get_stats(rp_scene *scene, rp_stats *out) {
 extern "C" rp_status rp_enable_timing(rp_scene *scene, int on) {
     if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
     scene->timing_on = on != 0;
+    scene->timer.only[0] = 0;
+    return RP_OK;
+}
+
+extern "C" rp_status rp_enable_timing_of(rp_scene *scene, const char *kernel) {
+    if (!scene) return fail(RP_ERR_INVALID_ARG, "null scene");
+    if (kernel && std::strlen(kernel) >= sizeof scene->timer.only)
+        return fail(RP_ERR_INVALID_ARG, "kernel name too long");
+    scene->timing_on = true;
+    if (kernel) std::strcpy(scene->timer.only, kernel);
+    else scene->timer.only[0] = 0;
     return RP_OK;
 }
 
@@ -1288,6 +1318,34 @@ extern "C" rp_status rp_guide_train_step(rp_guide *g, float lr, float *loss_out,
     return quantize(g, W.data(), amax);
 }
 
+extern "C" rp_status rp_guide_wait_selftest(rp_guide *g, uint64_t limit_ns) {
+    if (!g) return fail(RP_ERR_INVALID_ARG, "null guide");
+    if (limit_ns == 0 || limit_ns > 2000000000ull)
+        return fail(RP_ERR_INVALID_ARG, "limit_ns must be in (0, 2e9]");
+    RP_CUDA(cudaDeviceSynchronize(), "sync");
+    int prev = 0;
+    RP_CUDA(cudaMemcpy(&prev, g->err, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (prev) return fail(RP_ERR_TIMEOUT, "a tensor-core wait of the guide kernels timed out earlier");
+    int8_t *in = nullptr;
+    float *out = nullptr;
+    cudaError_t e = cudaMalloc((void **)&in, 128 * kGIn);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&out, 128 * kGOut * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(in, 0, 128 * kGIn);
+    GuideNet net{};
+    net.Wq = g->Wq;
+    for (int l = 0; l < 4; ++l) net.hid_scale[l] = 1.0f;
+    net.out_scale = 1.0f;
+    if (e == cudaSuccess) e = launch_guide_wait_selftest(net, in, out, g->err, limit_ns, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && err) e = cudaMemset(g->err, 0, sizeof(int));   // the expected timeout
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "guide wait self-test");
+    return err ? fail(RP_ERR_TIMEOUT, "the withheld tensor-core wait ran out (expected)") : RP_OK;
+}
+
 extern "C" rp_status rp_guide_status(rp_guide *g) {
     if (!g) return fail(RP_ERR_INVALID_ARG, "null guide");
     int err = 0;
@@ -1326,15 +1384,24 @@ struct rp_batch_s {
     std::vector<Item> items;
     rp_batch_config cfg{};
     unsigned long long *d_seeds = nullptr;
-    std::vector<Branch> br;
+    std::vector<Branch> br;          // graph mode: branches; persistent mode: job slots
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t nodes = 0;
+    // persistent mode: the jobs' launch arguments, the rounds' work counters
+    // and barrier, the timeout flag
+    LaunchArgs *d_jobs = nullptr;
+    unsigned int *d_ctrl = nullptr;
+    int *d_err = nullptr;
+    size_t jobs = 0, rounds = 0;
     ~rp_batch_s() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (fork) cudaEventDestroy(fork);
+        if (d_jobs) cudaFree(d_jobs);
+        if (d_ctrl) cudaFree(d_ctrl);
+        if (d_err) cudaFree(d_err);
         for (Branch &b : br) {
             for (void *p : b.allocs) cudaFree(p);
             if (b.s) cudaStreamDestroy(b.s);
@@ -1345,13 +1412,6 @@ struct rp_batch_s {
 };
 
 namespace {
-
-int device_sms() {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 152;
-}
 
 int popcount4(uint32_t m) { return __builtin_popcount(m & 127u); }
 
@@ -1367,6 +1427,106 @@ rp_status check_items(rp_scene *sc, const rp_batch_item *items, uint32_t n) {
         if (it.tech_mask == 0 || (it.tech_mask & ~RP_TECH_SEVEN)) return fail(RP_ERR_INVALID_ARG, "bad technique mask");
         if (rp_status s = guide_fits(sc, it.edit->E)) return s;
     }
+    return RP_OK;
+}
+
+// Persistent mode: every wave of every item's techniques and frames is a job
+// (launch arguments of its own, the wave buffers of a slot); jobs of the same
+// technique, frame and edit kind form rounds of up to cfg.streams jobs, and
+// each round is one cooperative launch of the persistent batch kernel
+// (k_batch.cuh) in the captured graph, after a reset of its work counters.
+rp_status batch_build_persistent(rp_batch *b, const rp_batch_item *items, bool motion) {
+    rp_scene *sc = b->sc;
+    const rp_batch_config &c = b->cfg;
+    const int D = sc->S.max_depth;
+    b->br.resize(c.streams);
+    for (rp_batch_s::Branch &sl : b->br)
+        if (rp_status s = alloc_wavebuf(sl.W, sl.allocs, c.wave_roots, D, motion)) return s;
+    struct Job {
+        LaunchArgs a;
+        int tech;
+    };
+    // jobs grouped by (frame, technique, mapped), in that order
+    std::map<std::tuple<int, int, int>, std::vector<Job>> groups;
+    const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
+    for (size_t i = 0; i < b->items.size(); ++i) {
+        const rp_batch_s::Item &it = b->items[i];
+        LaunchArgs a = base_args(sc, it.E, it.spp, items[i].seed, it.mask);
+        a.G = GuideLaunch{};
+        a.stats = nullptr;
+        a.timer = nullptr;
+        set_resolution(sc, a.S, it.W, it.H);
+        a.invN = (float)(1.0 / ((double)it.spp * it.W * it.H));
+        a.img = it.out;
+        a.residual = 1;
+        a.seed_dev = b->d_seeds + i;
+        const uint32_t N = it.spp * (uint32_t)(it.W * it.H);
+        for (int g = 1; g <= 2; ++g)
+            for (int t = 0; t < 7; ++t) {
+                if (!(it.mask & (1u << t)) || (t >= 4 && !it.E.motion)) continue;
+                const int mapped = (t >= 4 || it.E.motion) ? 1 : 0;
+                a.frame = g;
+                for (uint32_t r0 = 0; r0 < N; r0 += c.wave_roots) {
+                    a.root_begin = r0;
+                    a.root_end = std::min(N, r0 + c.wave_roots);
+                    groups[std::make_tuple(g, t, mapped)].push_back(Job{a, techs[t]});
+                }
+            }
+    }
+    // rounds: consecutive jobs of a group, job k of a round in slot k
+    std::vector<LaunchArgs> all;
+    struct Round {
+        size_t first;
+        int n, tech, mapped;
+    };
+    std::vector<Round> rounds;
+    for (auto &kv : groups) {
+        std::vector<Job> &js = kv.second;
+        for (size_t j0 = 0; j0 < js.size(); j0 += c.streams) {
+            const int nj = (int)std::min<size_t>(c.streams, js.size() - j0);
+            rounds.push_back(Round{all.size(), nj, js[j0].tech, std::get<2>(kv.first)});
+            for (int k = 0; k < nj; ++k) {
+                LaunchArgs a = js[j0 + k].a;
+                a.W = b->br[k].W;
+                all.push_back(a);
+            }
+        }
+    }
+    b->jobs = all.size();
+    b->rounds = rounds.size();
+    cudaError_t e = cudaMalloc((void **)&b->d_jobs, sizeof(LaunchArgs) * std::max<size_t>(all.size(), 1));
+    if (e == cudaSuccess && !all.empty())
+        e = cudaMemcpy(b->d_jobs, all.data(), sizeof(LaunchArgs) * all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ctrl, sizeof(unsigned int) * (kMaxBatchStages + 2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "batch job tables");
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(RP_ERR_CUDA, "stream creation failed");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (const Round &r : rounds) {
+        if (e != cudaSuccess) break;
+        BatchRound R{};
+        R.jobs = b->d_jobs + r.first;
+        R.n_jobs = r.n;
+        R.n_stages = batch_stages(r.tech, D, r.mapped != 0, R.stages);
+        R.work = b->d_ctrl;
+        R.bar = b->d_ctrl + kMaxBatchStages;
+        R.err = b->d_err;
+        R.chunk = 4 * kBlock;
+        e = cudaMemsetAsync(b->d_ctrl, 0, sizeof(unsigned int) * (kMaxBatchStages + 2), cs);
+        if (e == cudaSuccess) e = launch_batch_round(r.tech, R, (int)c.blocks_per_sm, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    cudaStreamDestroy(cs);
+    b->graph = graph;
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture of the persistent batch");
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+        return fail(RP_ERR_CUDA, "graph instantiation failed");
+    cudaGraphGetNodes(b->graph, nullptr, &b->nodes);
     return RP_OK;
 }
 
@@ -1399,6 +1559,13 @@ rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, cons
     c.streams = std::min<uint32_t>(c.streams, std::min<uint32_t>(8u, n));
     if (c.blocks_per_sm == 0) c.blocks_per_sm = 16;
     c.blocks_per_sm = std::min<uint32_t>(std::max<uint32_t>(c.blocks_per_sm, 1u), 64u);
+    c.persistent = c.persistent ? 1u : 0u;
+    if (c.persistent) {
+        // jobs per round (one wave buffer each): at most kMaxBatchJobs
+        c.streams = std::min<uint32_t>(std::max<uint32_t>(cfg_in && cfg_in->streams ? cfg_in->streams : 8u, 1u),
+                                       (uint32_t)kMaxBatchJobs);
+        if (!cfg_in || cfg_in->blocks_per_sm == 0) c.blocks_per_sm = 0;      // as many as fit
+    }
     b->cfg = c;
     auto bail = [&](rp_status s) { delete b; return s; };
     cudaError_t e = cudaMalloc((void **)&b->d_seeds, sizeof(unsigned long long) * n);
@@ -1407,6 +1574,11 @@ rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, cons
     for (uint32_t i = 0; i < n; ++i) seeds[i] = items[i].seed;
     e = cudaMemcpy(b->d_seeds, seeds.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(cuda_fail(e, "upload seeds"));
+    if (c.persistent) {
+        if (rp_status s = batch_build_persistent(b, items, motion)) return bail(s);
+        *out = b;
+        return RP_OK;
+    }
     // longest items first, each to the least loaded branch
     b->br.resize(c.streams);
     std::vector<uint32_t> order(n);
@@ -1437,7 +1609,7 @@ rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, cons
     for (rp_batch_s::Branch &br : b->br)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(br.s, b->fork, 0);
     const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
-    const int grid_q = (int)c.blocks_per_sm * device_sms();
+    const int grid_q = (int)c.blocks_per_sm * device_sm_count();
     for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
         const rp_batch_s::Item &it = b->items[i];
         rp_batch_s::Branch &br = b->br[it.branch];
@@ -1506,6 +1678,15 @@ extern "C" rp_status rp_batch_set_seeds(rp_batch *batch, const uint64_t *seeds, 
                             cudaMemcpyHostToDevice, (cudaStream_t)stream),
             "seed upload");
     return RP_OK;
+}
+
+extern "C" rp_status rp_batch_status(rp_batch *batch) {
+    if (!batch) return fail(RP_ERR_INVALID_ARG, "null batch");
+    RP_CUDA(cudaDeviceSynchronize(), "sync");
+    if (!batch->d_err) return RP_OK;
+    int err = 0;
+    RP_CUDA(cudaMemcpy(&err, batch->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    return err ? fail(RP_ERR_TIMEOUT, "a grid barrier of the persistent batch kernel timed out") : RP_OK;
 }
 
 extern "C" rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *graph_nodes) {

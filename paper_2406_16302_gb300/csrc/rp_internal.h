@@ -121,6 +121,15 @@ struct KernelTimer {
     int n = 0, cap = 0;
     cudaEvent_t *pool = nullptr;
     int pool_n = 0, pool_cap = 0, pool_used = 0;
+    char only[32] = {0};        // if set: only launches of the kernel of this name are timed
+    bool wants(const char *name) const {
+        if (!only[0]) return true;
+        for (int i = 0; i < 32; ++i) {
+            if (only[i] != name[i]) return false;
+            if (!name[i]) return true;
+        }
+        return true;
+    }
 };
 
 
@@ -163,14 +172,38 @@ struct LaunchArgs {
 // launchers implemented in the .cu files
 cudaError_t launch_residual(int tech, const LaunchArgs &a, cudaStream_t s);
 cudaError_t launch_primal(const LaunchArgs &a, cudaStream_t s);
+// closest hits of n rays; node visits, triangle tests and rays are added to
+// stats[ST_*] when stats is not null
 cudaError_t launch_trace(const DevScene &S, const DevEdit &E, int frame, uint32_t n,
                          const float *o, const float *d, float *t, int32_t *prim, float *b1,
-                         float *b2, cudaStream_t s);
+                         float *b2, unsigned long long *stats, cudaStream_t s);
 cudaError_t launch_philox(uint32_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                           cudaStream_t s);
+// streaming multiprocessors of the current device (cached per device)
+int device_sm_count();
 cudaError_t launch_add_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t s);
 // one wave [root_begin, root_end) of one technique (0 = primal path tracing)
 // in frame a.frame through the wavefront kernels
 cudaError_t launch_wave(int tech, const LaunchArgs &a, cudaStream_t s);
+
+// persistent batch kernel (k_batch.cu): one launch runs every stage of up to
+// kMaxBatchJobs waves (jobs) of one technique, frame and edit kind
+constexpr int kMaxBatchJobs = 128;
+constexpr int kMaxBatchStages = 64;
+struct BatchRound {
+    const LaunchArgs *jobs;     // [n_jobs] in device memory, each with its own wave buffers
+    int n_jobs;
+    int n_stages;
+    int2 stages[kMaxBatchStages];   // (stage kind, iteration), from batch_stages
+    unsigned int *work;         // [n_stages] work-item counters, zero at launch
+    unsigned int *bar;          // [2] grid barrier: arrivals, generation; zero at launch
+    int *err;                   // set when a barrier wait gave up
+    uint32_t chunk;             // elements (roots, rays, tasks) per work item
+};
+// the stage sequence of one wave (as run_wave launches it); returns its length
+int batch_stages(int tech, int D, bool mapped, int2 *out);
+// cooperative launch of one round; blocks_per_sm caps the blocks per SM
+// (0: as many as fit)
+cudaError_t launch_batch_round(int tech, const BatchRound &R, int blocks_per_sm, cudaStream_t s);
 
 }  // namespace rp

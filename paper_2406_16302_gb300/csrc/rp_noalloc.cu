@@ -27,8 +27,9 @@ namespace {
 
 constexpr size_t kMaxPixels = (size_t)RP_NOALLOC_MAX_PIXELS;
 
-// The scratch FP64 image: part of the library's device image, so every GPU
-// that loads the library holds it (24 MiB) until the process exits.
+// The scratch FP64 image: part of the library's device image.  A device holds
+// it (24 MiB) from the first call on it (lazy module loading, CUDA's default;
+// from library load with CUDA_MODULE_LOADING=EAGER) until the process exits.
 __device__ __align__(256) double g_scratch[kMaxPixels * 3];
 
 constexpr int kMaxDevices = 64;

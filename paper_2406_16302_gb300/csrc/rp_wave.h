@@ -35,6 +35,7 @@ enum { RF_ROOT_OK = 1, RF_GUIDE = 2 };
 
 constexpr int kMaxIter = 16;      // counter slots per queue
 
+
 struct WaveBuf {
     uint32_t R;                    // root capacity of a wave
     int S;                         // vertex slots per root
@@ -73,7 +74,26 @@ struct WaveBuf {
     float *m_w;                    // [3][qt] P_g(x), P_g'(y), J (for records)
     uint32_t *m_vis;               // [qt] 1 while none of the task's rays is blocked
     uint32_t *pend;                // [qt] tasks waiting for their rays
-    // counters: closest [kMaxIter], shadow [kMaxIter], tasks, rays, pending
+    // wavefront mapping: per task its mapping state, and the vertices the
+    // mapping replays (a pool; a task reserves one slot per path vertex)
+    uint32_t *ms_info;             // [qt] status | mode | dynamic index | step | replayed mask
+    float *ms_J;                   // [qt] Jacobian so far
+    uint32_t *ms_base;             // [qt] first pool slot of the task's replayed vertices
+    uint32_t *fin;                 // [qt] tasks whose mapping ended: accepted from the front,
+                                   // the others from the back
+    uint32_t yc;                   // pool capacity (vertices)
+    float *y_p, *y_n, *y_b;        // [3][yc] positions, [3][yc] normals, [2][yc] barycentrics
+    int *y_prim;                   // [yc]
+    // replay rays of the mapping (double-buffered queues of capacity qr)
+    // and their closest hits
+    uint32_t qr;
+    float *r_o[2], *r_d[2];        // [3][qr] each
+    int *r_ex[2];
+    uint32_t *r_task[2];
+    int *rh_prim;
+    float *rh_b1, *rh_b2, *rh_p;   // rh_p: [3][qr]
+    // counters: closest [kMaxIter], shadow [kMaxIter], tasks, rays, pending,
+    // replay rays [kMaxIter], pool slots, finished tasks (accepted, others)
     unsigned int *counts;
 };
 
@@ -82,6 +102,10 @@ __host__ __device__ __forceinline__ int cnt_shadow(int it) { return kMaxIter + i
 __host__ __device__ __forceinline__ int cnt_tasks() { return 2 * kMaxIter; }
 __host__ __device__ __forceinline__ int cnt_vis() { return 2 * kMaxIter + 1; }
 __host__ __device__ __forceinline__ int cnt_pend() { return 2 * kMaxIter + 2; }
-constexpr int kCountSlots = 2 * kMaxIter + 3;
+__host__ __device__ __forceinline__ int cnt_replay(int round) { return 2 * kMaxIter + 3 + round; }
+__host__ __device__ __forceinline__ int cnt_pool() { return 3 * kMaxIter + 3; }
+__host__ __device__ __forceinline__ int cnt_fin_acc() { return 3 * kMaxIter + 4; }
+__host__ __device__ __forceinline__ int cnt_fin_rej() { return 3 * kMaxIter + 5; }
+constexpr int kCountSlots = 3 * kMaxIter + 6;
 
 }  // namespace rp

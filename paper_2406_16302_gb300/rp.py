@@ -55,7 +55,8 @@ class rp_batch_item(C.Structure):
 
 
 class rp_batch_config(C.Structure):
-    _fields_ = [("wave_roots", C.c_uint32), ("streams", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
+    _fields_ = [("wave_roots", C.c_uint32), ("streams", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("persistent", C.c_uint32)]
 
 
 class rp_stats(C.Structure):
@@ -81,12 +82,13 @@ EXPORTS = ["rp_scene_create", "rp_scene_destroy", "rp_edit", "rp_edit_multi", "r
            "rp_render_primal", "rp_dump_samples", "rp_trace_closest", "rp_philox",
            "rp_bvh_build_host",
            "rp_enable_stats", "rp_get_stats", "rp_sync_status", "rp_enable_timing",
+           "rp_enable_timing_of",
            "rp_get_kernel_times",
            "rp_guide_create", "rp_guide_destroy", "rp_guide_set_weights", "rp_guide_get_weights",
            "rp_guide_set_int", "rp_guide_get_int", "rp_guide_infer", "rp_guide_encode", "rp_guide_loss_grad",
-           "rp_guide_train_step", "rp_guide_status", "rp_scene_set_guide",
+           "rp_guide_train_step", "rp_guide_status", "rp_guide_wait_selftest", "rp_scene_set_guide",
            "rp_batch_create", "rp_batch_destroy", "rp_batch_launch", "rp_batch_set_seeds",
-           "rp_batch_info", "rp_batch_autotune", "rp_scene_set_mapping",
+           "rp_batch_info", "rp_batch_status", "rp_batch_autotune", "rp_scene_set_mapping",
            "rp_last_error"]
 
 GUIDE_WEIGHTS, GUIDE_IN, GUIDE_OUT = 20480, 80, 48
@@ -124,6 +126,7 @@ def lib():
         "rp_sync_status": (I, [P]),
         "rp_bvh_build_host": (I, [P, C.c_uint32, P, C.c_uint32, P, C.c_uint32, P, P, P]),
         "rp_enable_timing": (I, [P, I]),
+        "rp_enable_timing_of": (I, [P, C.c_char_p]),
         "rp_get_kernel_times": (I, [P, P, I, P]),
         "rp_guide_create": (I, [P, U32, U64, P]),
         "rp_guide_destroy": (None, [P]),
@@ -135,12 +138,14 @@ def lib():
         "rp_guide_loss_grad": (I, [P, P, P, P, U32, P, P, P]),
         "rp_guide_train_step": (I, [P, C.c_float, P, P]),
         "rp_guide_status": (I, [P]),
+        "rp_guide_wait_selftest": (I, [P, U64]),
         "rp_scene_set_guide": (I, [P, P]),
         "rp_batch_create": (I, [P, P, U32, P, P]),
         "rp_batch_destroy": (None, [P]),
         "rp_batch_launch": (I, [P, P]),
         "rp_batch_set_seeds": (I, [P, P, P]),
         "rp_batch_info": (I, [P, P, P]),
+        "rp_batch_status": (I, [P]),
         "rp_batch_autotune": (I, [P, P, U32, U32, P, P]),
         "rp_scene_set_mapping": (I, [P, I]),
         "rp_last_error": (C.c_char_p, []),
@@ -352,6 +357,11 @@ def rp_enable_timing(scene: Scene, on=True):
     _check(lib().rp_enable_timing(scene.h, 1 if on else 0))
 
 
+def rp_enable_timing_of(scene: Scene, kernel=None):
+    """Time only the launches of one kernel (None: all)."""
+    _check(lib().rp_enable_timing_of(scene.h, kernel.encode() if kernel else None))
+
+
 def rp_get_kernel_times(scene: Scene) -> dict:
     """{kernel name: (launches, total ms)} since the previous call."""
     cap = 64
@@ -445,6 +455,13 @@ def rp_guide_status(guide: Guide):
 RP_MAPPING_OFF, RP_MAPPING_OBJECT, RP_MAPPING_CAMERA = 0, 1, 2
 
 
+def rp_guide_wait_selftest(guide: Guide, limit_ns=10_000_000):
+    """Run the inference kernel with its tensor-core completion withheld and
+    a wait bounded by limit_ns; raises RPError(RP_ERR_TIMEOUT) when the wait
+    ran out, as it should."""
+    _check(lib().rp_guide_wait_selftest(guide.h, limit_ns))
+
+
 def rp_scene_set_mapping(scene: Scene, mode=RP_MAPPING_CAMERA):
     """Path mapping mode (True means the default camera mode, False off)."""
     if mode is True:
@@ -468,7 +485,8 @@ def _batch_items(items):
 
 class Batch:
     """rp_batch_create / rp_batch_destroy.  items: list of
-    (Edit, width, height, spp, seed, tech_mask, float64 device image)."""
+    (Edit, width, height, spp, seed, tech_mask, float64 device image);
+    config: (wave_roots, streams, blocks_per_sm[, persistent])."""
 
     def __init__(self, scene: Scene, items, config=None):
         self.items = list(items)          # keeps edits and images alive
@@ -510,7 +528,13 @@ def rp_batch_info(batch: Batch):
     cfg = rp_batch_config()
     nodes = C.c_uint64()
     _check(lib().rp_batch_info(batch.h, C.byref(cfg), C.byref(nodes)))
-    return (cfg.wave_roots, cfg.streams, cfg.blocks_per_sm), int(nodes.value)
+    return (cfg.wave_roots, cfg.streams, cfg.blocks_per_sm, cfg.persistent), int(nodes.value)
+
+
+def rp_batch_status(batch: Batch):
+    """Raises RPError(RP_ERR_TIMEOUT) if a grid barrier of the persistent
+    batch kernel gave up (synchronises the device)."""
+    _check(lib().rp_batch_status(batch.h))
 
 
 def rp_batch_autotune(scene: Scene, items, spp_divisor=4):
@@ -519,7 +543,7 @@ def rp_batch_autotune(scene: Scene, items, spp_divisor=4):
     ms = C.c_double()
     _check(lib().rp_batch_autotune(scene.h, arr, len(items), int(spp_divisor), C.byref(cfg),
                                    C.byref(ms)))
-    return (cfg.wave_roots, cfg.streams, cfg.blocks_per_sm), float(ms.value)
+    return (cfg.wave_roots, cfg.streams, cfg.blocks_per_sm, cfg.persistent), float(ms.value)
 
 
 # ---------------------------------------------------------------------------
