@@ -229,8 +229,14 @@ def batch_workload(spp_scale=BATCH_SPP_SCALE):
 
 
 def run_batch(args):
-    """Batched edits: the autotuned batch as one CUDA graph launch per step,
-    against the same items rendered one by one."""
+    """Batched edits: 32 animation frames, each moving one object of 1k-200k
+    triangles at 256^2, 512^2 or 1024^2, at the configuration's spp divided by
+    batch_spp_scale.  The autotuned batch (a graph of per-wave launches, or
+    rounds of the persistent kernel) runs as one CUDA graph launch per step;
+    beside it the other batch mode, the same items rendered one by one, the
+    equal-time residual MSE of both on a sample of items against a converged
+    reference, and a stated subset of the items at the configuration's full
+    spp."""
     import dataclasses
     import torch
     from paper_2406_16302_gb300 import build, rp
@@ -248,26 +254,45 @@ def run_batch(args):
     t0 = time.perf_counter()
     cfg, tune_ms = rp.rp_batch_autotune(sc, items, spp_divisor=8)
     tune_s = time.perf_counter() - t0
-    batch = rp.Batch(sc, items, config=cfg)
-    _, nodes = rp.rp_batch_info(batch)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for w in range(args.warmup):
-        rp.rp_batch_launch(batch)
-    torch.cuda.synchronize()
-    times = []
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
+
+    def timed_launches(b, steps, warmup, seed_base, clk=None):
+        for w in range(warmup):
+            rp.rp_batch_launch(b)
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(steps):
             flush.zero_()
-            rp.rp_batch_set_seeds(batch, [100000 * (k + 1) + i for i in range(len(items))])
+            rp.rp_batch_set_seeds(b, [seed_base * (k + 1) + i for i in range(len(b.items))])
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rp.rp_batch_launch(batch)
+            rp.rp_batch_launch(b)
             e1.record(stream)
             torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-    ms = float(np.mean(times))
+            ts.append(e0.elapsed_time(e1))
+        rp.rp_batch_status(b)
+        return float(np.mean(ts))
+
+    def timed_render(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    batch = rp.Batch(sc, items, config=cfg)
+    _, nodes = rp.rp_batch_info(batch)
+    with ClockSampler(local) as clk:
+        ms = timed_launches(batch, args.steps, args.warmup, 100000)
+    # the other batch mode at its defaults
+    other_cfg = (1 << 20, 8, 0, 1) if not cfg[3] else (min(1 << 22, max(spp * w * h for _, w, h, spp in frames)), 1, 16, 0)
+    other = rp.Batch(sc, items, config=other_cfg)
+    other_ms = timed_launches(other, 2, 1, 200000)
+    del other
     # the same items one by one (each image size is a scene of its own camera)
     by_size = {}
     for _, w, h, _ in frames:
@@ -302,6 +327,69 @@ def run_batch(args):
             a_[0] += n
             a_[1] += t
         rp.rp_enable_timing(s2, False)
+    # equal-time residual MSE on a sample of items: the batch's image of one
+    # launch, the same item rendered alone with the same seed, against a
+    # reference of 16 renders at 4x the item's spp; MSE x time is constant for
+    # an unbiased estimator, so the equal-time ratio is MSE_b t_b / (MSE_1 t_1)
+    sample = list(range(0, len(frames), 8))
+    for o in outs:
+        o.zero_()
+    seeds = [300000 + i for i in range(len(items))]
+    rp.rp_batch_set_seeds(batch, seeds)
+    rp.rp_batch_launch(batch)
+    torch.cuda.synchronize()
+    mse = []
+    for i in sample:
+        f, w, h, spp = frames[i]
+        s2 = by_size[(w, h)]
+        e2 = rp.Edit(s2, f)
+        alone = rp.render_residual(s2, e2, spp, seeds[i])
+        ref = sum(rp.render_residual(s2, e2, 4 * spp, 400000 + 97 * i + r) for r in range(16)) / 16
+        mb = float(((outs[i] - ref) ** 2).mean().item())
+        m1 = float(((alone - ref) ** 2).mean().item())
+        scale = float(alone.abs().max().item()) or 1.0
+        mse.append({"item": i, "size": [w, h], "spp": spp, "mse_batch": mb, "mse_alone": m1,
+                    "max_diff_rel": float((outs[i] - alone).abs().max().item()) / scale})
+    mse_b = float(np.mean([m["mse_batch"] for m in mse]))
+    mse_1 = float(np.mean([m["mse_alone"] for m in mse]))
+    # a subset of the items at the configuration's full spp
+    _, full = batch_workload(1)
+    order = sorted(range(len(full)), key=lambda i: full[i][3] * full[i][1] * full[i][2])
+    subset, budget = [], 0
+    for i in order:
+        e, w, h, spp = full[i]
+        if budget + spp * w * h * 8 > 2.0e9:
+            break
+        subset.append(i)
+        budget += spp * w * h * 8
+    f_outs = [torch.zeros((full[i][2], full[i][1], 3), dtype=torch.float64, device="cuda")
+              for i in subset]
+    f_items = [(edits[i], full[i][1], full[i][2], full[i][3], 500000 + i, 15, f_outs[k])
+               for k, i in enumerate(subset)]
+    fb = rp.Batch(sc, f_items, config=cfg)
+    full_ms = timed_launches(fb, 1, 1, 600000)
+    del fb
+    # the same 32 edits as small items (128 x 128, 16 spp: one wave of 2^18
+    # roots per technique and frame, too small to fill the GPU alone): both
+    # batch modes at their defaults and the items one by one
+    small_scene = dataclasses.replace(scene, camera=dataclasses.replace(scene.camera, width=128,
+                                                                       height=128))
+    ssc = rp.Scene(small_scene)
+    s_edits = [rp.Edit(ssc, f[0]) for f in frames]
+    s_outs = [torch.zeros((128, 128, 3), dtype=torch.float64, device="cuda") for _ in frames]
+    s_items = [(s_edits[i], 128, 128, 16, 700000 + i, 15, s_outs[i]) for i in range(len(frames))]
+    small = {}
+    for name, c in (("graph", (1 << 18, 4, 16, 0)), ("persistent", (1 << 18, 32, 0, 1))):
+        b2 = rp.Batch(ssc, s_items, config=c)
+        small[name] = {"config": list(c), "ms": timed_launches(b2, 3, 1, 800000)}
+        del b2
+    t_one = 0.0
+    for i in range(len(frames)):
+        o = torch.zeros((128, 128, 3), dtype=torch.float64, device="cuda")
+        t_one += timed_render(lambda: rp.rp_render_residual(ssc, s_edits[i], 16, 900000 + i, o,
+                                                            stream=stream))
+    small["one_by_one"] = {"ms": t_one}
+    small["samples"] = 128 * 128 * 16 * 8 * len(frames)
     n_launch, ms_tot = kern["k_trace_closest"]
     bytes_total = (work["nodes_closest"] * BYTES_PER_NODE + work["tris_closest"] * BYTES_PER_TRI
                    + work["rays_closest"] * BYTES_PER_RAY["k_trace_closest"])
@@ -309,6 +397,8 @@ def run_batch(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_total / n_launch / (ms_tot / n_launch / 1e3) / 1e9
     value = samples / (ms / 1e3)
+    mode = "persistent" if cfg[3] else "graph"
+    launches = nodes // 2 if cfg[3] else int(sum(v[0] for v in kern.values()))
     line = {
         "metric": "residual samples/s", "value": value, "unit": "residual samples/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -319,16 +409,28 @@ def run_batch(args):
                    "spp": [spp for *_, spp in frames],
                    "spp_scale": f"the configuration's 64-256 spp divided by {args.batch_spp_scale}",
                    "samples_per_step": samples, "graph_nodes": nodes,
-                   "autotuned": {"wave_roots": cfg[0], "streams": cfg[1], "blocks_per_sm": cfg[2],
-                                 "proxy_ms": tune_ms, "tuning_s": tune_s},
+                   "autotuned": {"mode": mode, "wave_roots": cfg[0], "streams": cfg[1],
+                                 "blocks_per_sm": cfg[2], "proxy_ms": tune_ms, "tuning_s": tune_s},
                    "l2": "flushed between timed steps (256 MB write)"},
         "batch_vs_one_by_one": {"one_by_one_ms": seq_ms, "batch_ms": ms, "speedup": seq_ms / ms},
+        "batch_modes": {mode: {"config": list(cfg), "ms": ms},
+                        ("graph" if cfg[3] else "persistent"): {"config": list(other_cfg),
+                                                                "ms": other_ms}},
+        "equal_time_mse": {"items": mse, "reference": "16 renders at 4x the item's spp",
+                           "mse_batch": mse_b, "mse_one_by_one": mse_1,
+                           "ratio_at_equal_time": (mse_b * ms) / (mse_1 * seq_ms)},
+        "small_items": small,
+        "full_spp_subset": {"items": subset, "spp": [full[i][3] for i in subset],
+                            "resolutions": [full[i][1] for i in subset],
+                            "samples": budget, "ms": full_ms,
+                            "samples_per_s": budget / (full_ms / 1e3),
+                            "selection": "the smallest items by roots, up to 2e9 samples"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "kernel": "k_trace_closest",
                      "basis": "the items rendered one by one with per-kernel events",
                      "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (measured copy bandwidth)"},
         "cpu_baseline": None, "e2e": None,
-        "gpu_launches": int(sum(v[0] for v in kern.values())) * args.steps,
+        "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0:
@@ -392,6 +494,7 @@ def run_sweep(args):
         for i in range(R):
             ref += residual(4 * spp, 800000 + i, 127)[0]
         ref /= R
+        residual(spp, 809999, 15)                  # untimed: buffers at this root count
         row = dict(key)
         budget = None
         for name, mask, mapping in (("camera_4", 15, 2), ("object_4", 15, 1), ("off_4", 15, 0),
@@ -404,6 +507,7 @@ def run_sweep(args):
             t = float(np.mean(ts))
             budget = budget or t
             row[name] = {"mse": float(np.mean(ms)), "ms": t, "mse_at_budget": float(np.mean(ms)) * t / budget}
+        primal(1, spp, 829999)                  # untimed: allocates the primal wave buffers
         ms, ts = [], []
         for k in range(K):
             i2, ta = primal(2, spp, 820000 + k)
@@ -492,6 +596,16 @@ def equal_time_mse(rp, sc, ed, scene, spp, K=4, ref_renders=16, guide_iters=30, 
         ms.append(mse(i2 - i1)); ts.append(ta + tb)
     out["correlated_pt"] = {"spp": s_c, "mse": float(np.mean(ms)), "ms": float(np.mean(ts)),
                             "mse_at_budget": float(np.mean(ms)) * float(np.mean(ts)) / T}
+    # all seven techniques (the ghost techniques (4)-(6) added; without
+    # motion there is no ghost and this is the plain method again)
+    ms, ts = [], []
+    for k in range(K):
+        o7 = torch.zeros(sc.shape, dtype=torch.float64, device="cuda")
+        t = timed(lambda: rp.rp_render_residual(sc, ed, spp, 780000 + k, o7,
+                                               tech_mask=rp.RP_TECH_SEVEN, stream=stream))
+        ms.append(mse(o7)); ts.append(t)
+    out["seven_techniques"] = {"mse": float(np.mean(ms)), "ms": float(np.mean(ts)),
+                               "mse_at_budget": float(np.mean(ms)) * float(np.mean(ts)) / T}
     # learned proposal, trained online on the method's own samples
     box = scenes.guide_box(scene.dyn_vertices)
     batch = 1 << 20
@@ -516,7 +630,8 @@ def equal_time_mse(rp, sc, ed, scene, spp, K=4, ref_renders=16, guide_iters=30, 
                                   "batch": batch, "seconds": train_s,
                                   "loss_first_last": [losses[0], losses[-1]]}}
     out["ratios_at_budget"] = {k: out[k]["mse_at_budget"] / out["plain"]["mse_at_budget"]
-                               for k in ("guided", "pt_rerender", "correlated_pt")}
+                               for k in ("guided", "pt_rerender", "correlated_pt",
+                                         "seven_techniques") if k in out}
     return out
 
 
@@ -833,11 +948,24 @@ def main():
     def step(seed):
         rp.rp_render_residual(sc, ed, spp, seed, out, stream=stream)
 
-    for w in range(args.warmup):
+    # warm-up; the last warm-up step brackets every launch with events (the
+    # per-kernel breakdown), the timed steps only the dominant traversal
+    # kernel's launches (its roofline), so that the timed region carries few
+    # extra events
+    n_warm = max(1, args.warmup)                # the breakdown needs one warm-up step
+    for w in range(n_warm):
+        if w == n_warm - 1:
+            torch.cuda.synchronize()
+            rp.rp_get_kernel_times(sc)                     # discard
+            rp.rp_enable_timing(sc, True)
         step(seed0 + 1 + w)
     torch.cuda.synchronize()
-    rp.rp_get_kernel_times(sc)                     # discard
-    rp.rp_enable_timing(sc, True)
+    breakdown = rp.rp_get_kernel_times(sc)
+    rp.rp_enable_timing(sc, False)
+    trav = {"k_trace_closest": (work["nodes_closest"], work["tris_closest"], work["rays_closest"]),
+            "k_trace_shadow": (work["nodes_shadow"], work["tris_shadow"], work["rays_shadow"])}
+    dom = max(trav, key=lambda k: breakdown.get(k, (0, 0.0))[1])
+    rp.rp_enable_timing_of(sc, dom)
     step_ms = []
     kern = {}
     with ClockSampler(local) as clk:
@@ -864,7 +992,7 @@ def main():
     my_ms = float(np.mean(step_ms))
     worst_ms = max_over_ranks(my_ms, device="cuda")
     value = samples_per_step * ws / (worst_ms / 1e3)
-    launches_per_step = sum(n for n, _ in kern.values()) / args.steps
+    launches_per_step = sum(n for n, _ in breakdown.values())
 
     # end to end through the host-buffer entry point: edit upload, render,
     # image copy back, every step
@@ -888,12 +1016,9 @@ def main():
     # visits, triangle tests, queue entries) per launch over its CUDA-event
     # time, against the L2 read bandwidth when the BVH fits in L2 and the
     # HBM copy bandwidth otherwise; FP32 work against the FMA rate beside it
-    per_kernel = {k: {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
-                      "share": ms / max(sum(v[1] for v in kern.values()), 1e-9)}
-                  for k, (n, ms) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
-    trav = {"k_trace_closest": (work["nodes_closest"], work["tris_closest"], work["rays_closest"]),
-            "k_trace_shadow": (work["nodes_shadow"], work["tris_shadow"], work["rays_shadow"])}
-    dom = max(trav, key=lambda k: kern.get(k, (0, 0.0))[1])
+    total_ms = max(sum(v[1] for v in breakdown.values()), 1e-9)
+    per_kernel = {k: {"launches_per_step": n, "ms_per_step": ms, "share": ms / total_ms}
+                  for k, (n, ms) in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
     n_launch, ms_tot = kern[dom]
     launch_ms = ms_tot / n_launch
     nodes, tris, rays = trav[dom]
@@ -942,7 +1067,9 @@ def main():
                          "frac_of_measured": achieved_tf / probe["fp32_fma_tflops"],
                          "basis": f"{probe['sms']} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz; "
                                   f"{FLOP_PER_NODE} flop per node, {FLOP_PER_TRI} per triangle"},
-                "share_of_step": ms_tot / max(sum(v[1] for v in kern.values()), 1e-9)}
+                "share_of_step": breakdown[dom][1] / total_ms,
+                "timing": "the kernel's own launches bracketed by CUDA events on the render "
+                          "stream in every timed step (no other launch is)"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -969,6 +1096,8 @@ def main():
                    "samples_per_step": samples_per_step, "accumulation": "fp64 atomics",
                    "l2": "flushed between timed steps (256 MB write)",
                    "per_kernel": per_kernel,
+                   "per_kernel_basis": "one warm-up step with every launch bracketed by CUDA "
+                                       "events (not the timed steps)",
                    "rays_per_step": work["rays_closest"] + work["rays_shadow"],
                    "paths_per_step": work["paths"],
                    # splatted base paths per pixel (the paper's spp convention, Sec. 6)

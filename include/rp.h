@@ -480,9 +480,12 @@ rp_status rp_batch_status(rp_batch *batch);
 rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *graph_nodes);
 /* Autotuner: times candidate configurations on a proxy of the batch (each
  * item's spp divided by spp_divisor, outputs into a scratch image) by
- * coordinate descent over wave_roots (2^20 .. 2^23), streams (1, 2, 4) and
- * blocks_per_sm (8, 16, 32) from the defaults; writes the fastest and its
- * proxy time in ms.  Synchronous; leaves the items' images untouched. */
+ * coordinate descent in each batch mode: the graph mode over wave_roots
+ * (2^20 .. 2^23), streams (1, 2, 4) and blocks_per_sm (8, 16, 32); the
+ * persistent mode over wave_roots (2^18 .. 2^21), waves per round (4 .. 32,
+ * at most 2^23 roots in flight) and resident blocks per SM (all, 4, 2).
+ * Writes the fastest of both modes and its proxy time in ms.  Synchronous;
+ * leaves the items' images untouched. */
 rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *items, uint32_t n,
                             uint32_t spp_divisor, rp_batch_config *best, double *best_ms);
 

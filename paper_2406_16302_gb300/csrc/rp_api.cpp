@@ -106,6 +106,17 @@ struct rp_scene_s {
     KernelTimer timer;
     bool timing_on = false;
     int map_mode = 2;                 // path mapping mode (rp_scene_set_mapping)
+    // renders of few roots: their technique-and-frame waves run concurrently
+    // on these streams, each with wave buffers of its own
+    struct Lane {
+        WaveBuf W{};
+        std::vector<void *> allocs;
+        bool tasks = false;
+        cudaStream_t s = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<Lane> lanes;
+    cudaEvent_t lanes_fork = nullptr;
     // learned proposal of technique (3) and its per-root buffers
     rp_guide *guide = nullptr;
     int8_t *gin = nullptr;
@@ -130,6 +141,12 @@ struct rp_scene_s {
         if (d_stats) cudaFree(d_stats);
         if (d_scratch) cudaFree(d_scratch);
         free_wave();
+        for (Lane &l : lanes) {
+            for (void *p : l.allocs) cudaFree(p);
+            if (l.s) cudaStreamDestroy(l.s);
+            if (l.done) cudaEventDestroy(l.done);
+        }
+        if (lanes_fork) cudaEventDestroy(lanes_fork);
         for (int i = 0; i < timer.pool_n; ++i) cudaEventDestroy(timer.pool[i]);
         delete[] timer.pool;
         delete[] timer.entries;
@@ -762,6 +779,57 @@ static rp_status guide_fits(const rp_scene *sc, const DevEdit &E) {
     return RP_OK;
 }
 
+// A render of at most kLaneRoots roots per technique and frame is one wave
+// per technique and frame, too small to fill the GPU alone: its waves run on
+// kLanes streams at once, each stream with wave buffers of its own, forked
+// from and joined back into the caller's stream.  The waves are independent
+// (their own counters and queues), so the image is the sum of the same
+// samples as in sequence.
+constexpr uint32_t kLaneRoots = 1u << 20;
+constexpr int kLanes = 4;
+
+static rp_status render_lanes(rp_scene *sc, LaunchArgs a, uint32_t N, uint32_t mask, cudaStream_t st) {
+    const bool tasks = a.residual && a.E.motion;
+    if (sc->lanes.empty()) {
+        sc->lanes.resize(kLanes);
+        for (rp_scene::Lane &l : sc->lanes)
+            if (cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess)
+                return fail(RP_ERR_CUDA, "stream creation failed");
+        if (cudaEventCreateWithFlags(&sc->lanes_fork, cudaEventDisableTiming) != cudaSuccess)
+            return fail(RP_ERR_CUDA, "event creation failed");
+    }
+    const int D = sc->S.max_depth;
+    for (rp_scene::Lane &l : sc->lanes) {
+        if (l.W.R >= N && (!tasks || l.tasks)) continue;
+        // a lane's buffers are only reallocated once its stream is idle
+        RP_CUDA(cudaStreamSynchronize(l.s), "lane sync");
+        for (void *p : l.allocs) cudaFree(p);
+        l.allocs.clear();
+        l.tasks = tasks || l.tasks;
+        if (rp_status s = alloc_wavebuf(l.W, l.allocs, std::max(N, l.W.R), D, l.tasks)) return s;
+    }
+    RP_CUDA(cudaEventRecord(sc->lanes_fork, st), "fork");
+    for (rp_scene::Lane &l : sc->lanes) RP_CUDA(cudaStreamWaitEvent(l.s, sc->lanes_fork, 0), "fork");
+    const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
+    int k = 0;
+    a.root_begin = 0;
+    a.root_end = N;
+    for (int t = 0; t < 7; ++t)
+        for (int g = 1; g <= 2; ++g) {
+            if (!(mask & (1u << t)) || (t >= 4 && !a.E.motion)) continue;
+            rp_scene::Lane &l = sc->lanes[k++ % kLanes];
+            a.frame = g;
+            a.W = l.W;
+            RP_CUDA(launch_wave(techs[t], a, l.s), "wavefront launch");
+        }
+    for (rp_scene::Lane &l : sc->lanes) {
+        RP_CUDA(cudaEventRecord(l.done, l.s), "join");
+        RP_CUDA(cudaStreamWaitEvent(st, l.done, 0), "join");
+    }
+    return RP_OK;
+}
+
 static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint64_t seed,
                              uint32_t mask, double *d_out, cudaStream_t st) {
     if (rp_status s = guide_fits(sc, E)) return s;
@@ -777,6 +845,14 @@ static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint6
     // mask bits 0..6: techniques (1), (2), (3), path tracing, (4), (5), (6);
     // the ghost techniques need motion (without it there is no ghost)
     const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
+    int jobs = 0;
+    for (int t = 0; t < 7; ++t)
+        if ((mask & (1u << t)) && !(t >= 4 && !E.motion)) jobs += 2;
+    if (!sc->guide && N <= kLaneRoots && jobs >= 2) {
+        if (rp_status s = render_lanes(sc, a, N, mask, st)) return s;
+        sc->last_stream = st;
+        return RP_OK;
+    }
     for (int g = 1; g <= 2; ++g)
         for (int t = 0; t < 7; ++t) {
             if (!(mask & (1u << t)) || (t >= 4 && !E.motion)) continue;
@@ -1738,34 +1814,62 @@ extern "C" rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *ite
         ms = best_t;
         return RP_OK;
     };
-    // coordinate descent from the defaults over the wave size, the number
-    // of concurrent branches and the blocks per SM of the queue kernels
-    std::vector<uint32_t> waves;
+    // coordinate descent from the defaults of each batch mode, then the
+    // faster mode:
+    //  - graph mode over the wave size (2^20 .. 2^23), the concurrent branches
+    //    (1, 2, 4) and the blocks per SM of the queue kernels (8, 16, 32);
+    //  - persistent mode over the wave size (2^18 .. 2^21) and the waves per
+    //    round (4 .. 32) with at most 2^23 roots in flight, and the resident
+    //    blocks per SM (all that fit, 4, 2)
+    auto descend = [&](rp_batch_config cur, const std::vector<uint32_t> *vals, double &cur_ms,
+                       bool persistent) -> rp_status {
+        rp_status st2 = measure(cur, cur_ms);
+        for (int dim = 0; dim < 3 && st2 == RP_OK; ++dim)
+            for (uint32_t v : vals[dim]) {
+                rp_batch_config c = cur;
+                (dim == 0 ? c.wave_roots : dim == 1 ? c.streams : c.blocks_per_sm) = v;
+                if (c.wave_roots == cur.wave_roots && c.streams == cur.streams &&
+                    c.blocks_per_sm == cur.blocks_per_sm)
+                    continue;
+                if (persistent && (uint64_t)c.wave_roots * c.streams > (1ull << 23)) continue;
+                double ms = 0.0;
+                st2 = measure(c, ms);
+                if (st2 != RP_OK) break;
+                if (ms < cur_ms) { cur = c; cur_ms = ms; }
+            }
+        if (st2 == RP_OK) *best = cur;
+        return st2;
+    };
+    std::vector<uint32_t> gw[3], pw[3];
     for (uint32_t w = 1u << 20; w <= (1u << 23); w <<= 1) {
-        waves.push_back(w);
+        gw[0].push_back(w);
         if (w >= max_roots) break;
     }
-    const std::vector<uint32_t> streams = {1, 2, 4};
-    const std::vector<uint32_t> bps = {8, 16, 32};
-    rp_batch_config cur{};
-    cur.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, scene->wave_cap);
-    cur.streams = 1;
-    cur.blocks_per_sm = 16;
-    double cur_ms = 0.0;
-    rp_status s = measure(cur, cur_ms);
-    for (int dim = 0; dim < 3 && s == RP_OK; ++dim) {
-        const std::vector<uint32_t> &vals = dim == 0 ? waves : dim == 1 ? streams : bps;
-        for (uint32_t v : vals) {
-            rp_batch_config c = cur;
-            (dim == 0 ? c.wave_roots : dim == 1 ? c.streams : c.blocks_per_sm) = v;
-            if (c.wave_roots == cur.wave_roots && c.streams == cur.streams && c.blocks_per_sm == cur.blocks_per_sm)
-                continue;
-            double ms = 0.0;
-            s = measure(c, ms);
-            if (s != RP_OK) break;
-            if (ms < cur_ms) { cur = c; cur_ms = ms; }
-        }
+    gw[1] = {1, 2, 4};
+    gw[2] = {8, 16, 32};
+    for (uint32_t w = 1u << 18; w <= (1u << 21); w <<= 1) {
+        pw[0].push_back(w);
+        if (w >= max_roots) break;
     }
+    pw[1] = {4, 8, 16, 32};
+    pw[2] = {0, 4, 2};
+    rp_batch_config g0{};
+    g0.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, scene->wave_cap);
+    g0.streams = 1;
+    g0.blocks_per_sm = 16;
+    rp_batch_config p0{};
+    p0.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, 1u << 20);
+    p0.streams = 8;
+    p0.blocks_per_sm = 0;
+    p0.persistent = 1;
+    double g_ms = 0.0, p_ms = 0.0, cur_ms = 0.0;
+    rp_batch_config g_best{}, p_best{};
+    rp_status s = descend(g0, gw, g_ms, false);
+    if (s == RP_OK) g_best = *best;
+    if (s == RP_OK) s = descend(p0, pw, p_ms, true);
+    if (s == RP_OK) p_best = *best;
+    rp_batch_config cur = p_ms < g_ms ? p_best : g_best;
+    cur_ms = p_ms < g_ms ? p_ms : g_ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
