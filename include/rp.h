@@ -454,7 +454,7 @@ typedef struct {
                                     branches; 1: rounds of `streams` waves (jobs: one wave of
                                     one item's technique and frame, each with its own wave
                                     buffers), each round one cooperative launch of a
-                                    persistent kernel whose blocks pull (job, chunk) work
+                                    persistent kernel whose warps pull (job, chunk) work
                                     items of every stage from a device counter, with a
                                     grid barrier between stages */
 } rp_batch_config;

@@ -6,7 +6,7 @@
 // object, edit, image, seed, resolution) and its own wavefront buffers.  A
 // round is a set of jobs of the same technique, frame and edit kind, so they
 // share the stage sequence of run_wave (k_wave.cu).  One launch runs a whole
-// round: for every stage, the blocks pull work items (job, chunk of the
+// round: for every stage, the warps pull work items (job, chunk of the
 // stage's roots, rays or tasks) from a device counter and run the stage's
 // per-element work (wave_body.cuh); a grid barrier separates the stages.  The
 // launch is cooperative, so every block is resident and the barrier cannot
@@ -119,15 +119,19 @@ __device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, un
 
 }  // namespace
 
+// blocks per SM the persistent kernel is compiled for (its register budget)
+#ifndef RP_BATCH_MINBLOCKS
+#define RP_BATCH_MINBLOCKS 8
+#endif
+
 template <int T>
-__global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_batch(const __grid_constant__ BatchRound R) {
+__global__ void __launch_bounds__(kBlock, RP_BATCH_MINBLOCKS) k_batch(const __grid_constant__ BatchRound R) {
     __shared__ int s_stack[kStackDepth * kBlock];
     __shared__ float s_light[T == T_3 ? kT3LightSlots * 10 * kBlock : 1];
     __shared__ uint32_t s_n[kMaxBatchJobs];          // elements of each job in this stage
     __shared__ uint32_t s_first[kMaxBatchJobs + 1];  // first work item of each job
-    __shared__ uint32_t s_item;
     const uint32_t chunk = R.chunk;
-    Vtx x[kMaxVerts], y[kMaxVerts];
+    Vtx x[kMaxVerts];
     for (int s = 0; s < R.n_stages; ++s) {
         const int kind = R.stages[s].x, it = R.stages[s].y;
         for (int j = threadIdx.x; j < R.n_jobs; j += blockDim.x) s_n[j] = stage_elems(R.jobs[j], kind, it);
@@ -142,11 +146,13 @@ __global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_batch(const __gr
         }
         __syncthreads();
         const uint32_t items = s_first[R.n_jobs];
+        // each warp pulls its own work items: no block-wide wait inside a
+        // stage, so a warp never idles behind another warp's longest ray
+        const int lane = threadIdx.x & 31;
         for (;;) {
-            if (threadIdx.x == 0) s_item = atomicAdd(R.work + s, 1u);
-            __syncthreads();
-            const uint32_t w = s_item;
-            __syncthreads();
+            uint32_t w = 0u;
+            if (lane == 0) w = atomicAdd(R.work + s, 1u);
+            w = __shfl_sync(0xffffffffu, w, 0);
             if (w >= items) break;
             int j = 0;
             while (s_first[j + 1] <= w) ++j;
@@ -154,15 +160,14 @@ __global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_batch(const __gr
             Ctx c(A, s_stack + threadIdx.x);
             BodyState st{};
             st.x = x;
-            st.y = y;
             st.s_light = s_light;
             const uint32_t e0 = (w - s_first[j]) * chunk, e1 = min(s_n[j], e0 + chunk);
             if (kind == SK_CLEAR) {
-                if (threadIdx.x == 0) stage_element<T>(A, c, st, kind, it, 0u);
+                if (lane == 0) stage_element<T>(A, c, st, kind, it, 0u);
             } else {
-                for (uint32_t i = e0 + threadIdx.x; i < e1; i += blockDim.x)
-                    stage_element<T>(A, c, st, kind, it, i);
+                for (uint32_t i = e0 + lane; i < e1; i += 32u) stage_element<T>(A, c, st, kind, it, i);
             }
+            __syncwarp();
         }
         if (!grid_barrier(R.bar, R.bar + 1, gridDim.x, R.err)) return;
     }

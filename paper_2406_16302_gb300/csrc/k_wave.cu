@@ -296,10 +296,9 @@ __global__ void __launch_bounds__(kBlock, RP_MAPFIN_MINBLOCKS) k_map_fin(const _
     Ctx c(A, s_stack + threadIdx.x);
     const uint32_t n_acc = min(A.W.counts[cnt_fin_acc()], A.W.qt);
     const uint32_t n = min(n_acc + A.W.counts[cnt_fin_rej()], A.W.qt);
-    Vtx x[kMaxVerts], y[kMaxVerts];
+    Vtx x[kMaxVerts];
     BodyState st{};
     st.x = x;
-    st.y = y;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
         map_fin_body(A, c, st, j, 0);
 

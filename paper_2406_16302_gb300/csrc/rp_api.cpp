@@ -86,6 +86,12 @@ struct rp_guide_s {
     }
 };
 
+// roots per wave of a render (the wave buffers scale with it; ray tags
+// hold 24 bits of wave-local root)
+#ifndef RP_WAVE_ROOTS
+#define RP_WAVE_ROOTS (1u << 22)
+#endif
+
 struct rp_scene_s {
     DevScene S{};
     std::vector<DevObject> objects;   // 0: the dynamic mesh; k >= 1: static triangle ranges
@@ -102,7 +108,7 @@ struct rp_scene_s {
     WaveBuf W{};
     std::vector<void *> wave_allocs;
     bool wave_tasks = false;
-    uint32_t wave_cap = 1u << 22;  // roots per wave
+    uint32_t wave_cap = RP_WAVE_ROOTS;  // roots per wave
     KernelTimer timer;
     bool timing_on = false;
     int map_mode = 2;                 // path mapping mode (rp_scene_set_mapping)
@@ -785,8 +791,11 @@ static rp_status guide_fits(const rp_scene *sc, const DevEdit &E) {
 // from and joined back into the caller's stream.  The waves are independent
 // (their own counters and queues), so the image is the sum of the same
 // samples as in sequence.
+#ifndef RP_LANES
+#define RP_LANES 4
+#endif
 constexpr uint32_t kLaneRoots = 1u << 20;
-constexpr int kLanes = 4;
+constexpr int kLanes = RP_LANES;
 
 static rp_status render_lanes(rp_scene *sc, LaunchArgs a, uint32_t N, uint32_t mask, cudaStream_t st) {
     const bool tasks = a.residual && a.E.motion;
@@ -1590,7 +1599,7 @@ rp_status batch_build_persistent(rp_batch *b, const rp_batch_item *items, bool m
         R.work = b->d_ctrl;
         R.bar = b->d_ctrl + kMaxBatchStages;
         R.err = b->d_err;
-        R.chunk = 4 * kBlock;
+        R.chunk = 128;             // elements per work item of one warp
         e = cudaMemsetAsync(b->d_ctrl, 0, sizeof(unsigned int) * (kMaxBatchStages + 2), cs);
         if (e == cudaSuccess) e = launch_batch_round(r.tech, R, (int)c.blocks_per_sm, cs);
     }

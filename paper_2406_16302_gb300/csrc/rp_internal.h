@@ -198,7 +198,7 @@ struct BatchRound {
     unsigned int *work;         // [n_stages] work-item counters, zero at launch
     unsigned int *bar;          // [2] grid barrier: arrivals, generation; zero at launch
     int *err;                   // set when a barrier wait gave up
-    uint32_t chunk;             // elements (roots, rays, tasks) per work item
+    uint32_t chunk;             // elements (roots, rays, tasks) per work item of one warp
 };
 // the stage sequence of one wave (as run_wave launches it); returns its length
 int batch_stages(int tech, int D, bool mapped, int2 *out);

@@ -52,7 +52,7 @@ namespace rp {
 struct BodyState {
     PathCounts pc;
     unsigned int roots, accepted;
-    Vtx *x, *y;                 // path vertex arrays (kMaxVerts) of the mapping kernels
+    Vtx *x;                     // a path vertex array (kMaxVerts) of the mapping kernels
     float *s_light;             // technique (3)'s shared light-side values
 };
 
@@ -626,41 +626,59 @@ __device__ __forceinline__ uint32_t append_n(unsigned int *counter, uint32_t k) 
     return g.shfl(base, 0) + ex;
 }
 
-// Stage C3 for base path x (n vertices) of task ti, mapped to y with `mi`:
-// its value, and both splats of the two-way estimator (Eq. shiftmapped;
-// R3).  A rejected or invalid pair emits the one-way value now.  An accepted
-// pair needs the mapped path's edges to be clear (replayed edges are clear by
-// construction, unchanged edges are tested against the dynamic objects
-// only): those rays are queued for k_trace_vis and the task waits for
-// k_map_b; when the queue is full they are traced here.
-__device__ void finish_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t ti, uint32_t root,
-                            int tech, int sa, int sb, const Vtx *y, MapInfo mi) {
-    const LaunchArgs &A = c.A;
-    const WaveBuf &W = A.W;
-    const int g = A.frame, g2 = 3 - g;
+// Stage C3, the base path's side: f(x), the balance denominator P_g(x) and
+// the one-way value of base path x (n vertices); false when f(x) = 0 (the
+// path adds nothing).
+struct XSide {
+    float3 fx, v1;
     int pa, ex;
-    const float3 fx = path_throughput(c, g, x, n, pa, ex);
-    if (zero3(fx)) return;
+    SF Pg;
+    uint32_t searched, crossed;
+};
+
+__device__ bool finish_x(Ctx &c, PathCounts &pc, const Vtx *x, int n, XSide &xs) {
+    const LaunchArgs &A = c.A;
+    const int g = A.frame;
+    xs.fx = path_throughput(c, g, x, n, xs.pa, xs.ex);
+    if (zero3(xs.fx)) return false;
     ++pc.paths;
-    const float invN = A.invN;
     const float sign = (g == 2) ? 1.0f : -1.0f;
     // the ghost terms of P_g(x) search x's edges against the objects at
     // their frame-g' pose: the same query as the dynamic-only visibility of
     // an edge the mapping leaves unchanged
-    uint32_t searched = 0u, crossed = 0u;
-    const SF Pg = mis_denominator(c, g, x, n, &searched, &crossed);
-    const float3 v1 = fx * ldexpf(sign * invN / Pg.m, ex - Pg.e);     // one-way value
+    xs.searched = 0u;
+    xs.crossed = 0u;
+    xs.Pg = mis_denominator(c, g, x, n, &xs.searched, &xs.crossed);
+    xs.v1 = xs.fx * ldexpf(sign * A.invN / xs.Pg.m, xs.ex - xs.Pg.e);     // one-way value
+    return true;
+}
+
+// Stage C3, the mapped path's side, for base path x of task ti (its side in
+// xs) mapped to y with `mi` (y is read only when the pair is accepted);
+// `same` holds the edges the mapping leaves unchanged.  Both splats of the
+// two-way estimator (Eq. shiftmapped; R3).  A rejected or invalid pair emits
+// the one-way value now.  An accepted pair needs the mapped path's edges to
+// be clear (replayed edges are clear by construction, unchanged edges are
+// tested against the dynamic objects only): those rays are queued for
+// k_trace_vis and the task waits for k_map_b; when the queue is full they
+// are traced here.
+__device__ void finish_y(Ctx &c, PathCounts &pc, const XSide &xs, const Vtx *y, int n, uint32_t same,
+                         uint32_t ti, uint32_t root, int tech, int sa, int sb, MapInfo mi) {
+    const LaunchArgs &A = c.A;
+    const WaveBuf &W = A.W;
+    const int g = A.frame, g2 = 3 - g;
+    const float invN = A.invN;
+    const float sign = (g == 2) ? 1.0f : -1.0f;
+    const float3 fx = xs.fx, v1 = xs.v1;
+    const int pa = xs.pa, ex = xs.ex;
+    const SF Pg = xs.Pg;
+    const uint32_t searched = xs.searched;
     int pb = -1, ey = 0;
     float3 fy = f3(0, 0, 0);
     SF Py{0.f, 0};
-    uint32_t same = 0u;              // edges the mapping leaves unchanged
-    if (mi.status == MAP_ACCEPT) {
-        for (int j = 0; j + 1 < n; ++j)
-            if (same3(x[j].p, y[j].p) && same3(x[j + 1].p, y[j + 1].p)) same |= 1u << j;
-        // an unchanged edge that crosses the objects at their frame-g' pose
-        // blocks the mapped path
-        if (same & crossed) mi.status = MAP_INVALID;
-    }
+    // an unchanged edge that crosses the objects at their frame-g' pose
+    // blocks the mapped path
+    if (mi.status == MAP_ACCEPT && (same & xs.crossed)) mi.status = MAP_INVALID;
     if (mi.status == MAP_ACCEPT) {
         fy = path_throughput(c, g2, y, n, pb, ey);
         // an unchanged edge of y crosses nothing at the frame-g pose: it is
@@ -737,6 +755,18 @@ __device__ void finish_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_
     W.m_vis[ti] = 1u;
     const uint32_t p = append(W.counts + cnt_pend());
     W.pend[p] = ti;                   // p < qt: one entry per task at most
+}
+
+// stage C3 for base path x and its mapped path y held in separate arrays
+__device__ void finish_task(Ctx &c, PathCounts &pc, const Vtx *x, int n, uint32_t ti, uint32_t root,
+                            int tech, int sa, int sb, const Vtx *y, MapInfo mi) {
+    XSide xs;
+    if (!finish_x(c, pc, x, n, xs)) return;
+    uint32_t same = 0u;              // edges the mapping leaves unchanged
+    if (mi.status == MAP_ACCEPT)
+        for (int j = 0; j + 1 < n; ++j)
+            if (same3(x[j].p, y[j].p) && same3(x[j + 1].p, y[j + 1].p)) same |= 1u << j;
+    finish_y(c, pc, xs, y, n, same, ti, root, tech, sa, sb, mi);
 }
 
 // the whole of stages C1-C3 for one task in one thread (tasks that find the
@@ -1187,29 +1217,43 @@ __device__ __forceinline__ void map_fin_body(const LaunchArgs &A, Ctx &c, BodySt
     const WaveBuf &W = A.W;
     const uint32_t n_acc = min(W.counts[cnt_fin_acc()], W.qt);
     const int g2 = 3 - A.frame;
-    Vtx *x = st.x, *y = st.y;
-    do {
-        const uint32_t ti = W.fin[j < n_acc ? j : W.qt - 1u - (j - n_acc)];
-        const uint32_t w = W.ms_info[ti];
-        const int4 t = W.tasks[ti];
-        const PathRef P = task_path(A, ti);
-        const int k = assemble(c, P.r, P.lay, P.sa, P.sb, x);
-        MapInfo mi;
-        mi.status = (int)ms_status(w);
-        mi.J = W.ms_J[ti];
-        mi.replayed = 0u;
-        if (mi.status == MAP_ACCEPT) {
-            const uint32_t base = W.ms_base[ti];
-            const uint32_t rep = ms_replayed(w);
-            mi.replayed = rep;
-            for (int j = 0; j < k; ++j) {
-                if ((rep >> j) & 1u) y[j] = pool_load(c, W, base + (uint32_t)j);
-                else if (!ms_camera(w) && j == ms_dyn(w)) y[j] = make_vertex(c, g2, x[j].prim, x[j].b1, x[j].b2);
-                else y[j] = x[j];
+    Vtx *x = st.x;
+    const uint32_t ti = W.fin[j < n_acc ? j : W.qt - 1u - (j - n_acc)];
+    const uint32_t w = W.ms_info[ti];
+    const int4 t = W.tasks[ti];
+    const PathRef P = task_path(A, ti);
+    const int k = assemble(c, P.r, P.lay, P.sa, P.sb, x);
+    MapInfo mi;
+    mi.status = (int)ms_status(w);
+    mi.J = W.ms_J[ti];
+    mi.replayed = 0u;
+    XSide xs;
+    if (!finish_x(c, pc, x, k, xs)) return;
+    uint32_t same = 0u;
+    if (mi.status == MAP_ACCEPT) {
+        // the mapped path overwrites the base path in the one array: its
+        // replayed vertices from the pool, the transformed dynamic vertex,
+        // the others unchanged; `vs` marks the unchanged vertices
+        const uint32_t base = W.ms_base[ti];
+        const uint32_t rep = ms_replayed(w);
+        mi.replayed = rep;
+        uint32_t vs = 0u;
+        for (int q = 0; q < k; ++q) {
+            if ((rep >> q) & 1u) {
+                const Vtx yq = pool_load(c, W, base + (uint32_t)q);
+                if (same3(x[q].p, yq.p)) vs |= 1u << q;
+                x[q] = yq;
+            } else if (!ms_camera(w) && q == ms_dyn(w)) {
+                const Vtx yq = make_vertex(c, g2, x[q].prim, x[q].b1, x[q].b2);
+                if (same3(x[q].p, yq.p)) vs |= 1u << q;
+                x[q] = yq;
+            } else {
+                vs |= 1u << q;
             }
         }
-        finish_task(c, pc, x, k, ti, A.root_begin + P.r, t.y, t.z, t.w, y, mi);
-    } while (0);
+        same = vs & (vs >> 1) & ((1u << (k - 1)) - 1u);
+    }
+    finish_y(c, pc, xs, x, k, same, ti, A.root_begin + P.r, t.y, t.z, t.w, mi);
 }
 
 
