@@ -474,6 +474,12 @@ static __device__ bool traverse(const DevBVH &B, float3 o, float3 d, float tmin,
                          int *overflow, int id_add = 0, int skip_lo = 0, int skip_n = 0,
                          const uint32_t *skip_bits = nullptr) {
     if (B.n_nodes == 0) return false;
+    // a ray with a non-finite component (the direction of two coincident
+    // vertices) hits no triangle, but fminf/fmaxf drop its NaN slabs, so its
+    // box tests would pass and it would walk most of the tree: stop here
+    if (!(isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
+          isfinite(d.z)))
+        return false;
     const WtRay w = wt_setup(d);
     const float3 id = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float3 oid = f3(o.x * id.x, o.y * id.y, o.z * id.z);
@@ -710,6 +716,9 @@ static __device__ int traverse_all(const DevBVH &B, float3 o, float3 d, float tm
                                    float *ts, int *prims, int maxh, int *stack, Counters &cnt,
                                    int *overflow, int id_add) {
     if (B.n_nodes == 0) return 0;
+    if (!(isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
+          isfinite(d.z)))
+        return 0;                 // no crossings (see traverse)
     const WtRay w = wt_setup(d);
     const float3 id = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float3 oid = f3(o.x * id.x, o.y * id.y, o.z * id.z);
