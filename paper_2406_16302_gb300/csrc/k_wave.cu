@@ -10,10 +10,14 @@
 //   identity edits) the mapping is the identity and the path is evaluated and
 //   splatted here with no ray at all; with motion every non-static path
 //   becomes a mapping task.
-// Stage C (motion):  k_map_a, one thread per mapping task: object
-//   transform, camera replay, reconnection or random replay in the other
-//   frame, two-way MIS; the mapped path's edges that need a visibility test
-//   go to a queue traced by k_trace_vis, and k_map_b emits the pairs.
+// Stage C (motion):  the path mapping as queued rounds: k_map_start runs
+//   each task's mapping program (object transform or camera replay, then
+//   per walk vertex unchanged, reconnection or random replay) until it
+//   needs a replay ray; k_trace_map traces the round's replay rays in the
+//   other frame and k_map_step resumes the tasks with their hits.  k_map_fin
+//   evaluates base and mapped paths with two-way MIS; the mapped path's
+//   edges that need a visibility test go to a queue traced by k_trace_vis,
+//   and k_map_b emits the pairs.
 //
 // The random numbers, walk termination rules and path enumeration are those
 // of the one-thread-per-root kernels (rp_device.cuh), so both modes produce
