@@ -33,6 +33,7 @@ int batch_stages(int tech, int D, bool mapped, int2 *out) {
         add(SK_ENUM, 0);
         add(SK_MAP_START, 0);
         for (int r = 0; r < D - 1 && r + 1 < kMaxIter; ++r) {
+            add(SK_REPLAY_DIR, r);
             add(SK_TRACE_MAP, r);
             add(SK_MAP_STEP, r);
         }

@@ -24,7 +24,7 @@ namespace {
 
 enum StageKind {
     SK_CLEAR = 0, SK_GEN, SK_START, SK_SHADOW, SK_CLOSEST, SK_EXTEND, SK_ENUM, SK_EVAL,
-    SK_MAP_START, SK_TRACE_MAP, SK_MAP_STEP, SK_MAP_FIN, SK_TRACE_VIS, SK_MAP_B
+    SK_MAP_START, SK_TRACE_MAP, SK_MAP_STEP, SK_MAP_FIN, SK_TRACE_VIS, SK_MAP_B, SK_REPLAY_DIR
 };
 
 constexpr uint64_t kBarrierNs = 2000000000ull;      // a barrier wait gives up after 2 s
@@ -48,6 +48,7 @@ __device__ __forceinline__ uint32_t stage_elems(const LaunchArgs &A, int kind, i
     case SK_CLOSEST: return min(__ldcg(W.counts + cnt_closest(it)), W.qc);
     case SK_EXTEND: return min(__ldcg(W.counts + cnt_closest(it - 1)), W.qc);
     case SK_MAP_START: return min(__ldcg(W.counts + cnt_tasks()), W.qt);
+    case SK_REPLAY_DIR:
     case SK_TRACE_MAP:
     case SK_MAP_STEP: return min(__ldcg(W.counts + cnt_replay(it)), W.qr);
     case SK_MAP_FIN:
@@ -77,6 +78,7 @@ __device__ __forceinline__ void stage_element(const LaunchArgs &A, Ctx &c, BodyS
         if constexpr (T == T_1 || T == T_2 || T == T_3 || T == T_PT) eval_fast_body<T>(A, c, st, i, 0);
         break;
     case SK_MAP_START: map_start_body(A, c, st, i, 0); break;
+    case SK_REPLAY_DIR: replay_dir_body(A, c, st, i, it); break;
     case SK_TRACE_MAP: trace_map_body(A, c, st, i, it); break;
     case SK_MAP_STEP: map_step_body(A, c, st, i, it); break;
     case SK_MAP_FIN: map_fin_body(A, c, st, i, 0); break;

@@ -13,8 +13,9 @@
 // Stage C (motion):  the path mapping as queued rounds: k_map_start runs
 //   each task's mapping program (object transform or camera replay, then
 //   per walk vertex unchanged, reconnection or random replay) until it
-//   needs a replay ray; k_trace_map traces the round's replay rays in the
-//   other frame and k_map_step resumes the tasks with their hits.  k_map_fin
+//   needs a replay ray; k_replay_dir finds the round's replay directions,
+//   k_trace_map traces the replay rays in the other frame and k_map_step
+//   resumes the tasks with their hits.  k_map_fin
 //   evaluates base and mapped paths with two-way MIS; the mapped path's
 //   edges that need a visibility test go to a queue traced by k_trace_vis,
 //   and k_map_b emits the pairs.
@@ -258,7 +259,17 @@ __global__ void __launch_bounds__(kBlock, RP_MAP_MINBLOCKS) k_map_start(const __
     }
 }
 
-// stage C2a: closest hits of the mapping's replay rays of one round, in the
+// stage C2a: the directions of the round's random-seed replays (double
+// precision, one thread per queued replay)
+__global__ void __launch_bounds__(kBlock, RP_MAP_MINBLOCKS) k_replay_dir(const __grid_constant__ LaunchArgs A, int round) {
+    Ctx c(A, nullptr);
+    const uint32_t n = min(A.W.counts[cnt_replay(round)], A.W.qr);
+    BodyState st{};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        replay_dir_body(A, c, st, i, round);
+}
+
+// stage C2b: closest hits of the mapping's replay rays of one round, in the
 // other frame
 __global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_trace_map(const __grid_constant__ LaunchArgs A, int round) {
     __shared__ int s_stack[kStackDepth * kBlock];
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(kBlock, RP_TRACE_MINBLOCKS) k_trace_map(const 
     }
 }
 
-// stage C2b: resume the tasks of one round with their hits; the next
+// stage C2c: resume the tasks of one round with their hits; the next
 // replay rays go to round + 1
 __global__ void __launch_bounds__(kBlock, RP_MAP_MINBLOCKS) k_map_step(const __grid_constant__ LaunchArgs A, int round) {
     __shared__ int s_stack[kStackDepth * kBlock];
@@ -422,6 +433,7 @@ void map_stage(const LaunchArgs &a, cudaStream_t s, int gQ) {
     // ray and the walk vertices x_2 .. x_{k-2})
     const int rounds = a.S.max_depth - 1;
     for (int r = 0; r < rounds && r + 1 < kMaxIter; ++r) {
+        RP_LAUNCH("k_replay_dir", gQ, kBlock, k_replay_dir, a, r);
         RP_LAUNCH("k_trace_map", gQ, kBlock, k_trace_map, a, r);
         RP_LAUNCH("k_map_step", gQ, kBlock, k_map_step, a, r);
     }

@@ -189,7 +189,10 @@ cudaError_t launch_wave(int tech, const LaunchArgs &a, cudaStream_t s);
 // persistent batch kernel (k_batch.cu): one launch runs every stage of up to
 // kMaxBatchJobs waves (jobs) of one technique, frame and edit kind
 constexpr int kMaxBatchJobs = 128;
-constexpr int kMaxBatchStages = 64;
+// stages of one wave at the largest depth (kMaxDepth = 10, motion): clear,
+// generate, 3 root steps, 3 per walk iteration (11), enumerate, map start,
+// 3 per mapping round (9), finish, visibility, pairs = 70
+constexpr int kMaxBatchStages = 72;
 struct BatchRound {
     const LaunchArgs *jobs;     // [n_jobs] in device memory, each with its own wave buffers
     int n_jobs;

@@ -20,8 +20,9 @@
 // Stage C (motion):  the path mapping as queued rounds: k_map_start runs
 //   each task's mapping program (object transform or camera replay, then
 //   per walk vertex unchanged, reconnection or random replay) until it
-//   needs a replay ray; k_trace_map traces the round's replay rays in the
-//   other frame and k_map_step resumes the tasks with their hits.  k_map_fin
+//   needs a replay ray; k_replay_dir finds the round's replay directions,
+//   k_trace_map traces the replay rays in the other frame and k_map_step
+//   resumes the tasks with their hits.  k_map_fin
 //   evaluates base and mapped paths with two-way MIS; the mapped path's
 //   edges that need a visibility test go to a queue traced by k_trace_vis,
 //   and k_map_b emits the pairs.
@@ -994,6 +995,27 @@ __device__ __forceinline__ bool push_replay(const LaunchArgs &A, int round, floa
     return true;
 }
 
+// The direction of the random-seed replay of step (a, b, cc) of task P in
+// state w (Sec. 5): the step's sampling routine inverted at x_a for the
+// direction to x_b, then run at y_a with the numbers found (double
+// precision); false when that direction is invalid.
+__device__ bool replay_direction(Ctx &c, const PathRef &P, uint32_t w, uint32_t base, int a, int b,
+                                 int cc, float3 &w2) {
+    const LaunchArgs &A = c.A;
+    const int g = A.frame, g2 = 3 - g;
+    const Vtx xa = xv(c, P, a), ya = yv(c, P, w, base, a), xb = xv(c, P, b);
+    const float3 wo = unit3(xb.p - xa.p);
+    double u1, u2;
+    if (cc < 0) {
+        cosine_inverse(xa.n, wo, u1, u2);
+        w2 = cosine_dir(A.S, ya.n, u1, u2);
+        return dot3(ya.n, w2) > 0.f;
+    }
+    const Vtx xc = xv(c, P, cc), yc = yv(c, P, w, base, cc);
+    bsdf_inverse(get_mat(c, g, xa.mat), xa.n, unit3(xc.p - xa.p), wo, u1, u2);
+    return bsdf_sample(A.S, get_mat(c, g2, ya.mat), ya.n, unit3(yc.p - ya.p), u1, u2, w2);
+}
+
 // the tests and Jacobian factor of replayed vertex nb = y[b] (map_step after
 // its trace); stores nb in the pool.  Returns MAP_ACCEPT to go on.
 __device__ uint32_t replay_hit(Ctx &c, const PathRef &P, uint32_t &w, uint32_t base, float &J, int a,
@@ -1058,30 +1080,24 @@ __device__ void map_run(Ctx &c, const PathRef &P, uint32_t ti, uint32_t w, uint3
         if (same3(ya.p, xa.p)) continue;            // predecessor unchanged: y_b = x_b
         const Vtx xb = xv(c, P, b);
         if (reconnect_ok(c, g, xa, g2, ya, g, xb)) continue;    // keep the vertex
-        // random-seed replay through the inverse of the step's sampling routine
-        const float3 wo = unit3(xb.p - xa.p);
-        double u1, u2;
-        float3 w2;
-        if (cc < 0) {
-            cosine_inverse(xa.n, wo, u1, u2);
-            w2 = cosine_dir(A.S, ya.n, u1, u2);
-            if (dot3(ya.n, w2) <= 0.f) { st = MAP_INVALID; break; }
-        } else {
-            const Vtx xc = xv(c, P, cc), yc = yv(c, P, w, base, cc);
-            bsdf_inverse(get_mat(c, g, xa.mat), xa.n, unit3(xc.p - xa.p), wo, u1, u2);
-            if (!bsdf_sample(A.S, get_mat(c, g2, ya.mat), ya.n, unit3(yc.p - ya.p), u1, u2, w2)) {
-                st = MAP_INVALID;
-                break;
-            }
-        }
-        // a replay queued into `round` is traced only if that round runs
-        // (rounds 0 .. max_depth - 2, see map_stage)
-        if (round < A.S.max_depth - 1 && round < kMaxIter && push_replay(A, round, ya.p, w2, ya.prim, ti)) {
+        // random-seed replay: queued with its direction still to be found
+        // (k_replay_dir computes the directions of a whole round's queue at
+        // once, so that the double-precision inversion runs with every lane
+        // of a warp busy); a replay queued into `round` is traced only if
+        // that round runs (rounds 0 .. max_depth - 2, see map_stage)
+        const float nan = __int_as_float(0x7fc00000);
+        if (round < A.S.max_depth - 1 && round < kMaxIter &&
+            push_replay(A, round, ya.p, f3(nan, nan, nan), ya.prim, ti)) {
             W.ms_info[ti] = ms_with_step(ms_with_status(w, kRunning), s);
             W.ms_J[ti] = J;
             return;
         }
-        // queue full: trace here
+        // queue full: the direction and the trace here
+        float3 w2;
+        if (!replay_direction(c, P, w, base, a, b, cc, w2)) {
+            st = MAP_INVALID;
+            break;
+        }
         Vtx nb{};
         const bool hit = trace_next(c, g2, ya, w2, nb);
         st = replay_hit(c, P, w, base, J, a, b, cc, w2, hit, nb);
@@ -1152,6 +1168,27 @@ __device__ __forceinline__ void map_start_body(const LaunchArgs &A, Ctx &c, Body
             continue;
         }
         map_run(c, P, ti, (uint32_t)i << 5, base, 1.0f, 0);
+    } while (0);
+}
+
+
+// the per-element work of k_replay_dir: the direction of replay ray i of
+// round `it` whose direction is still to be found (a NaN there; the camera
+// rays of the camera replay carry theirs).  An invalid direction stays NaN:
+// its trace finds no hit, and k_map_step ends the task as MAP_INVALID, as
+// the replay's own step would have.
+__device__ __forceinline__ void replay_dir_body(const LaunchArgs &A, Ctx &c, BodyState &st, uint32_t i, int it) {
+    const WaveBuf &W = A.W;
+    const int bq = it & 1;
+    do {
+        if (!isnan(W.r_d[bq][i])) continue;
+        const uint32_t ti = W.r_task[bq][i];
+        const PathRef P = task_path(A, ti);
+        const uint32_t w = W.ms_info[ti];
+        int a, b, cc;
+        map_program(ms_camera(w), ms_dyn(w), P.k, ms_step(w), a, b, cc);
+        float3 w2;
+        if (replay_direction(c, P, w, W.ms_base[ti], a, b, cc, w2)) store3(W.r_d[bq], W.qr, i, w2);
     } while (0);
 }
 
