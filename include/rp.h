@@ -447,7 +447,8 @@ typedef struct {
     uint32_t wave_roots;         /* roots per wave (0: min(largest item, 2^22)) */
     uint32_t streams;            /* graph mode: concurrent branches, 1..8 (0: 1);
                                     persistent mode: waves per round, 1..128 (0: 8) */
-    uint32_t blocks_per_sm;      /* graph mode: grid of the queue kernels per SM, 1..64 (0: 16);
+    uint32_t blocks_per_sm;      /* graph mode: grid of the queue kernels per SM, 1..128 (0: one
+                                    block per 256 roots of a wave, 16..128 per SM);
                                     persistent mode: at most this many resident blocks per
                                     SM (0: as many as fit) */
     uint32_t persistent;         /* 0: a graph of per-wave kernel launches over `streams`
@@ -481,7 +482,7 @@ rp_status rp_batch_info(rp_batch *batch, rp_batch_config *config, uint64_t *grap
 /* Autotuner: times candidate configurations on a proxy of the batch (each
  * item's spp divided by spp_divisor, outputs into a scratch image) by
  * coordinate descent in each batch mode: the graph mode over wave_roots
- * (2^20 .. 2^23), streams (1, 2, 4) and blocks_per_sm (8, 16, 32); the
+ * (2^20 .. 2^23), streams (1, 2, 4) and blocks_per_sm (0, 16, 32, 64, 128); the
  * persistent mode over wave_roots (2^18 .. 2^21), waves per round (4 .. 32,
  * at most 2^23 roots in flight) and resident blocks per SM (all, 4, 2).
  * Writes the fastest of both modes and its proxy time in ms.  Synchronous;

@@ -1645,8 +1645,7 @@ rp_status batch_build(rp_scene *sc, const rp_batch_item *items, uint32_t n, cons
     c.wave_roots = std::max<uint32_t>(c.wave_roots, 256u);
     if (c.streams == 0) c.streams = 1;
     c.streams = std::min<uint32_t>(c.streams, std::min<uint32_t>(8u, n));
-    if (c.blocks_per_sm == 0) c.blocks_per_sm = 16;
-    c.blocks_per_sm = std::min<uint32_t>(std::max<uint32_t>(c.blocks_per_sm, 1u), 64u);
+    c.blocks_per_sm = std::min<uint32_t>(c.blocks_per_sm, 128u);     // 0: by the wave's roots
     c.persistent = c.persistent ? 1u : 0u;
     if (c.persistent) {
         // jobs per round (one wave buffer each): at most kMaxBatchJobs
@@ -1829,7 +1828,8 @@ extern "C" rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *ite
     // coordinate descent from the defaults of each batch mode, then the
     // faster mode:
     //  - graph mode over the wave size (2^20 .. 2^23), the concurrent branches
-    //    (1, 2, 4) and the blocks per SM of the queue kernels (8, 16, 32);
+    //    (1, 2, 4) and the blocks per SM of the queue kernels (by the wave's
+    //    roots, 16, 32, 64, 128);
     //  - persistent mode over the wave size (2^18 .. 2^21) and the waves per
     //    round (4 .. 32) with at most 2^23 roots in flight, and the resident
     //    blocks per SM (all that fit, 4, 2)
@@ -1858,7 +1858,7 @@ extern "C" rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *ite
         if (w >= max_roots) break;
     }
     gw[1] = {1, 2, 4};
-    gw[2] = {8, 16, 32};
+    gw[2] = {0, 16, 32, 64, 128};
     for (uint32_t w = 1u << 18; w <= (1u << 21); w <<= 1) {
         pw[0].push_back(w);
         if (w >= max_roots) break;
@@ -1868,7 +1868,7 @@ extern "C" rp_status rp_batch_autotune(rp_scene *scene, const rp_batch_item *ite
     rp_batch_config g0{};
     g0.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, scene->wave_cap);
     g0.streams = 1;
-    g0.blocks_per_sm = 16;
+    g0.blocks_per_sm = 0;
     rp_batch_config p0{};
     p0.wave_roots = (uint32_t)std::min<uint64_t>(max_roots, 1u << 20);
     p0.streams = 8;

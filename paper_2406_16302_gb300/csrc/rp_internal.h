@@ -153,7 +153,7 @@ struct LaunchArgs {
     uint32_t root_begin, root_end;
     uint64_t seed;
     const unsigned long long *seed_dev;   // if set, the seed is read from device memory
-    int grid_q;                 // blocks of the queue kernels (0: 16 per SM)
+    int grid_q;                 // blocks of the queue kernels (0: by the wave's roots)
     float invN;                 // 1 / (spp * W * H)
     int tech_mask;
     double *img;                // accumulation image or null

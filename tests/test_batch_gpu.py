@@ -156,7 +156,7 @@ def test_autotune_picks_a_candidate_and_keeps_the_result(rp):
     if cfg[3]:            # persistent mode: waves per round, resident blocks per SM
         assert cfg[1] in (4, 8, 16, 32) and cfg[2] in (0, 2, 4) and cfg[0] * cfg[1] <= 1 << 23
     else:                 # graph mode: branches, queue-kernel blocks per SM
-        assert cfg[1] in (1, 2, 4) and cfg[2] in (8, 16, 32) and cfg[0] >= 256
+        assert cfg[1] in (1, 2, 4) and cfg[2] in (0, 16, 32, 64, 128) and cfg[0] >= 256
     for o in outs:
         assert float(o.abs().sum()) == 0.0          # the autotuner leaves the images alone
     b1 = rp.Batch(base, items, config=cfg)
