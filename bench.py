@@ -64,8 +64,8 @@ TRAFFIC_CAPTURE = {
                               "sources_sha": "ca6e970db6ab6a9a"},
     # the 72 launches of one 16 spp render (2^24-root waves, as at 256 spp)
     "terrain_motion_1024": {"kernel": "k_trace_closest",
-                            "dram_bytes_per_ray": (22153.879808e6 + 4247.311616e6) / 223016348.0,
-                            "sources_sha": "853f5c28c0eb18e1"},
+                            "dram_bytes_per_ray": (22141.595136e6 + 4245.214464e6) / 223016348.0,
+                            "sources_sha": "1cf54bc4495f0d71"},
 }
 KERNEL_SOURCES = ["rp_device.cuh", "wave_body.cuh", "k_wave.cu", "rp_internal.h", "rp_wave.h"]
 
