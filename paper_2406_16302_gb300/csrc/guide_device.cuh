@@ -18,10 +18,12 @@ namespace rp {
 // reduction 2^f ch - 2 rintf(2^f ch / 2) is exact (|2^f ch| <= 32, and an
 // even integer subtracted from it leaves a representable value), and the
 // low part 2^f cl adds a rounding of at most one ulp of r.  sin(pi r) and
-// cos(pi r) are then taken in single precision: their error in 128 e stays
-// below 1e-4, so the quantised value is the one the double-precision sine
-// gives unless 128 e lies within 1e-3 of a rounding boundary, where it is
-// recomputed in double from the exact argument.
+// cos(pi r) are then taken in single precision: r is within 2^-24 of the
+// exact reduced argument and sincospif within one ulp of the sine and cosine
+// of its argument, so 128 e is within 128 (pi 2^-24 + 2^-24) < 3.2e-5 of
+// its double-precision value, and the quantised value is the one the
+// double-precision sine gives unless 128 e lies within 2.5e-4 of a rounding
+// boundary, where it is recomputed in double from the exact argument.
 static __device__ void guide_encode_d(const float *box, double3 p, float3 n, int8_t *m) {
     double u[3] = {((double)p.x - box[0]) * box[3], ((double)p.y - box[1]) * box[4],
                    ((double)p.z - box[2]) * box[5]};
@@ -34,7 +36,7 @@ static __device__ void guide_encode_d(const float *box, double3 p, float3 n, int
     };
     auto near_half = [](float e) {
         const float v = 128.0f * e;
-        return fabsf(v - floorf(v) - 0.5f) < 1e-3f;
+        return fabsf(v - floorf(v) - 0.5f) < 2.5e-4f;
     };
     for (int v = 0; v < 2; ++v)
         for (int c = 0; c < 3; ++c) {
@@ -63,12 +65,18 @@ static __device__ void guide_encode_d(const float *box, double3 p, float3 n, int
     m[79] = 0;
 }
 
-// The mixture weights and concentrations in single precision (they only
-// scale values and pick a lobe); the lobe directions in double, because the
-// density exp(kappa (mu.w - 1)) multiplies the error of mu.w - 1 by kappa
-// (up to 493).
+// The mixture in single precision.  The density exp(kappa (mu.w - 1))
+// multiplies the error of mu.w - 1 by kappa (up to 493), so it is taken as
+// exp(-kappa |mu - w|^2 / 2) (the same for unit vectors), whose argument
+// has no cancellation: a rounding of mu or w moves |mu - w|^2 by a small
+// fraction of itself, or by about 1e-7 |mu - w| across it, and the density
+// stays within about 2e-5 of the double-precision value wherever
+// kappa |mu - w|^2 / 2 < 20 (beyond that a lobe adds less than e^-20).  The
+// sampled direction itself stays in double (guide_lobe_dir_d,
+// vmf_sample_d): in single precision 0.1 % of a guided technique's paths
+// moved beyond 1e-4 of the oracle's.
 struct MixF {
-    double3 mu[kGLobes];
+    float3 mu[kGLobes];
     float kappa[kGLobes], pi[kGLobes], norm[kGLobes];   // norm = kappa / (2 pi (1 - e^-2kappa))
 };
 
@@ -88,21 +96,30 @@ static __device__ void guide_mixture_f(const float *o, MixF &M) {
 #pragma unroll
     for (int j = 0; j < kGLobes; ++j) {
         M.pi[j] *= inv;
-        const double3 m = d3(o[5 * j], o[5 * j + 1], o[5 * j + 2]);
-        const double l = sqrt(ddot(m, m));
-        M.mu[j] = l > 1e-12 ? dscale(m, 1.0 / l) : d3(0.0, 0.0, 1.0);
+        const float3 m = f3(o[5 * j], o[5 * j + 1], o[5 * j + 2]);
+        const float l = sqrtf(dot3(m, m));
+        M.mu[j] = l > 1e-12f ? m * (1.f / l) : f3(0.f, 0.f, 1.f);
         const float k = expf(fminf(6.2f, fmaxf(-4.0f, o[5 * j + 3])));
         M.kappa[j] = k;
         M.norm[j] = k / (2.f * kPi * -expm1f(-2.f * k));
     }
 }
 
-static __device__ __forceinline__ float mix_pdf_f(const MixF &M, double3 w) {
+static __device__ __forceinline__ float mix_pdf_f(const MixF &M, float3 wf) {
     float p = 0.f;
 #pragma unroll
-    for (int j = 0; j < kGLobes; ++j)
-        p += M.pi[j] * M.norm[j] * expf(M.kappa[j] * (float)(ddot(M.mu[j], w) - 1.0));
+    for (int j = 0; j < kGLobes; ++j) {
+        const float3 d = M.mu[j] - wf;
+        p += M.pi[j] * M.norm[j] * expf(-0.5f * M.kappa[j] * dot3(d, d));
+    }
     return p;
+}
+
+// the direction of lobe j, normalised in double (for sampling it)
+static __device__ double3 guide_lobe_dir_d(const float *o, int j) {
+    const double3 m = d3(o[5 * j], o[5 * j + 1], o[5 * j + 2]);
+    const double l = sqrt(ddot(m, m));
+    return l > 1e-12 ? dscale(m, 1.0 / l) : d3(0.0, 0.0, 1.0);
 }
 
 // inversion of the vMF cosine CDF (Jakob 2012) and a uniform azimuth in the
@@ -118,7 +135,6 @@ static __device__ double3 vmf_sample_d(const DevScene &S, double3 mu, double kap
     tangent_frame_d(mu, t, b);
     return dadd(dadd(dscale(t, s * cp), dscale(b, s * sp)), dscale(mu, c));
 }
-
 
 // transpose of the linear part of a 3x4 row-major transform times a
 static __device__ __forceinline__ double3 dlinear_T(const float *M, double3 a) {

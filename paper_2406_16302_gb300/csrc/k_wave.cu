@@ -128,18 +128,20 @@ __global__ void __launch_bounds__(256) k_start3g(const __grid_constant__ LaunchA
                 acc += mix.pi[i];
                 if (v < acc) { j = i; break; }
             }
-            wl = vmf_sample_d(A.S, mix.mu[j], (double)mix.kappa[j], u.x, u.y);
+            wl = vmf_sample_d(A.S, guide_lobe_dir_d(A.G.gout + (size_t)r * kGOut, j),
+                              (double)mix.kappa[j], u.x, u.y);
             w = dlinear(M, wl);
         }
         const double cw = ddot(nw, w);
         const float pc = cw > 0.0 ? (float)(cw / kPiD) : 0.f;
-        const float pv = mix_pdf_f(mix, wl);
+        const float3 wlf = tof(wl);
+        const float pv = mix_pdf_f(mix, wlf);
         A.G.gratio[r] = pc / (0.5f * pc + 0.5f * pv);
         const uint32_t slot = guide_slot(A.G, g, root);
         if (slot != ~0u) {
             const uint32_t C = A.G.smp.cap;
-            A.G.smp.w[slot] = (float)wl.x; A.G.smp.w[C + slot] = (float)wl.y;
-            A.G.smp.w[2 * C + slot] = (float)wl.z;
+            A.G.smp.w[slot] = wlf.x; A.G.smp.w[C + slot] = wlf.y;
+            A.G.smp.w[2 * C + slot] = wlf.z;
         }
         const float3 wf = tof(w);
         if (dot3(xD.n, wf) > 0.f) push_closest(A, 0, 0, xD.p, wf, xD.prim, make_tag(r, SIDE_LIGHT, 1));
