@@ -64,8 +64,8 @@ TRAFFIC_CAPTURE = {
                               "sources_sha": "ca6e970db6ab6a9a"},
     # the 72 launches of one 16 spp render (2^24-root waves, as at 256 spp)
     "terrain_motion_1024": {"kernel": "k_trace_closest",
-                            "dram_bytes_per_ray": (22141.595136e6 + 4245.214464e6) / 223016348.0,
-                            "sources_sha": "1cf54bc4495f0d71"},
+                            "dram_bytes_per_ray": (22144.531712e6 + 4244.507392e6) / 223016348.0,
+                            "sources_sha": "7b5999697f545cd7"},
 }
 KERNEL_SOURCES = ["rp_device.cuh", "wave_body.cuh", "k_wave.cu", "rp_internal.h", "rp_wave.h"]
 

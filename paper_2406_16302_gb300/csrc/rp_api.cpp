@@ -670,10 +670,12 @@ static rp_status check_render(rp_scene *sc, uint32_t spp, uint32_t mask) {
 
 // wavefront buffers for waves of up to R roots; `tasks` adds the mapping
 // task queue needed by edits with motion
-static rp_status ensure_guide_buffers(rp_scene *sc) {
-    if (!sc->guide || sc->guide_R >= sc->W.R) return RP_OK;
+// the learned proposal's per-root buffers (features, outputs, p_cos / q)
+// for waves of up to R roots
+static rp_status ensure_guide_buffers(rp_scene *sc, uint32_t R_need) {
+    if (!sc->guide || sc->guide_R >= R_need) return RP_OK;
     sc->free_guide_buffers();
-    const size_t R = sc->W.R;
+    const size_t R = R_need;
     cudaError_t e = cudaMalloc((void **)&sc->gin, R * kGIn);
     if (e == cudaSuccess) e = cudaMalloc((void **)&sc->gout, R * kGOut * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&sc->gratio, R * sizeof(float));
@@ -682,7 +684,7 @@ static rp_status ensure_guide_buffers(rp_scene *sc) {
         return e == cudaErrorMemoryAllocation ? fail(RP_ERR_OOM, "guide buffer allocation failed")
                                               : cuda_fail(e, "cudaMalloc guide buffers");
     }
-    sc->guide_R = sc->W.R;
+    sc->guide_R = R_need;
     return RP_OK;
 }
 
@@ -753,13 +755,13 @@ static rp_status alloc_wavebuf(WaveBuf &W, std::vector<void *> &allocs, uint32_t
 
 static rp_status ensure_wave(rp_scene *sc, uint32_t R, bool tasks) {
     const int D = sc->S.max_depth;
-    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return ensure_guide_buffers(sc);
+    if (sc->W.R >= R && (!tasks || sc->wave_tasks)) return ensure_guide_buffers(sc, sc->W.R);
     R = std::max(R, sc->W.R);
     tasks = tasks || sc->wave_tasks;
     sc->free_wave();
     if (rp_status s = alloc_wavebuf(sc->W, sc->wave_allocs, R, D, tasks)) return s;
     sc->wave_tasks = tasks;
-    return ensure_guide_buffers(sc);
+    return ensure_guide_buffers(sc, sc->W.R);
 }
 
 // run roots [r0, r1) of technique `tech` (0: primal) in frame a.frame as waves
@@ -821,16 +823,30 @@ static rp_status render_lanes(rp_scene *sc, LaunchArgs a, uint32_t N, uint32_t m
         l.tasks = tasks || l.tasks;
         if (rp_status s = alloc_wavebuf(l.W, l.allocs, std::max(N, l.W.R), D, l.tasks)) return s;
     }
+    // with the learned proposal, technique (3)'s two waves share the scene's
+    // guide buffers, so they run one after the other on one lane
+    const bool guided = sc->guide && (mask & RP_TECH_DYNAMIC_TWO_ENDS);
+    if (guided) {
+        if (rp_status s = ensure_guide_buffers(sc, N)) return s;
+        a.G.gin = sc->gin;
+        a.G.gout = sc->gout;
+        a.G.gratio = sc->gratio;
+    }
     RP_CUDA(cudaEventRecord(sc->lanes_fork, st), "fork");
     for (rp_scene::Lane &l : sc->lanes) RP_CUDA(cudaStreamWaitEvent(l.s, sc->lanes_fork, 0), "fork");
     const int techs[7] = {1, 2, 3, 7, 4, 5, 6};
-    int k = 0;
+    int k = 0, t3_lane = -1;
     a.root_begin = 0;
     a.root_end = N;
     for (int t = 0; t < 7; ++t)
         for (int g = 1; g <= 2; ++g) {
             if (!(mask & (1u << t)) || (t >= 4 && !a.E.motion)) continue;
-            rp_scene::Lane &l = sc->lanes[k++ % kLanes];
+            int li = k++ % kLanes;
+            if (guided && techs[t] == 3) {
+                if (t3_lane < 0) t3_lane = li;
+                li = t3_lane;
+            }
+            rp_scene::Lane &l = sc->lanes[li];
             a.frame = g;
             a.W = l.W;
             RP_CUDA(launch_wave(techs[t], a, l.s), "wavefront launch");
@@ -860,7 +876,7 @@ static rp_status render_into(rp_scene *sc, const DevEdit &E, uint32_t spp, uint6
     int jobs = 0;
     for (int t = 0; t < 7; ++t)
         if ((mask & (1u << t)) && !(t >= 4 && !E.motion)) jobs += 2;
-    if (!sc->guide && N <= kLaneRoots && jobs >= 2) {
+    if (N <= kLaneRoots && jobs >= 2) {
         if (rp_status s = render_lanes(sc, a, N, mask, st)) return s;
         sc->last_stream = st;
         return RP_OK;
